@@ -1,0 +1,212 @@
+"""Seeded synthetic inputs for rank-constrained SCM estimation.
+
+This module only draws random numbers and assembles the method's INPUTS; it
+contains none of the estimator's arithmetic (no setup, no EM update, no Wiener
+filter).  Both the CUDA path and the FP64 oracle consume what it returns.
+
+The paper's data (JNAS speech convolved with measured room impulse responses,
+Sec. IV-A) is not available, so seeded draws with the same STFT scale stand in
+for it (fs = 16 kHz, Table II):
+
+* target direction: a plane wave from a random direction of arrival,
+  a_true[i, m] = exp(-j 2 pi f_i tau_m) / sqrt(M) (unit norm);
+* diffuse noise SCM: spherically isotropic coherence sin(z)/z with
+  z = 2 pi f_i d_mn / c, plus 1e-3 I (full rank);
+* target variance: rank-K NMF, r_h = T V with T, V ~ Gamma(1, 1);
+* noise variance: r_u ~ Gamma(shape 2, scale 0.5), i.i.d. per slot;
+* x = a_true s + u, s ~ N_c(0, r_h), u ~ N_c(0, r_u R_true) (Sec. II-B-1).
+
+A stand-in for the ILRMA stage (Sec. II-A) gives the boundary inputs: the true
+demixing matrix W_true = Q^H (Q unitary, first column a_true) perturbed by 1 %
+complex Gaussian noise; a is the target column of W~^{-1}; R' is the
+back-projected rank-(M-1) noise SCM of Eq. (eq:rit); r_u0 follows Eq.
+(eq:ruinit) and r_h0 is the true NMF product with 1 % multiplicative noise
+(stands in for Eq. (eq:rhinit)).  The target index n_h is 0.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+FS = 16000.0          # sampling frequency [Hz] (Table II)
+C_SOUND = 343.0       # speed of sound [m/s]
+BASE_SEED = 190801964
+ALPHA = 1.1           # inverse-gamma shape (Table II)
+BETA = 1e-16          # inverse-gamma scale (Table II)
+
+
+@dataclass
+class ProblemSpec:
+    """Shape and geometry of one utterance (one STFT tensor I x J x M)."""
+    M: int
+    I: int
+    J: int
+    K: int = 10
+    geometry: str = "linear"     # "linear" (spacing) or "circular" (radius)
+    spacing: float = 0.04        # [m]: mic spacing, or radius if circular
+
+    @property
+    def nfft(self) -> int:
+        return 2 * (self.I - 1)
+
+
+@dataclass
+class Workload:
+    """A named set of utterances solved together, plus the iteration count."""
+    name: str
+    specs: List[ProblemSpec]
+    n_iter: int
+    seed: int
+    note: str = ""
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def slots(self) -> int:
+        return int(sum(s.I * s.J for s in self.specs))
+
+
+def _mic_positions(spec: ProblemSpec) -> np.ndarray:
+    M = spec.M
+    if spec.geometry == "linear":
+        xs = (np.arange(M) - (M - 1) / 2.0) * spec.spacing
+        return np.stack([xs, np.zeros(M)], axis=1)
+    if spec.geometry == "circular":
+        ang = 2.0 * np.pi * np.arange(M) / M
+        return spec.spacing * np.stack([np.cos(ang), np.sin(ang)], axis=1)
+    raise ValueError(f"unknown geometry {spec.geometry!r}")
+
+
+def make_problem(spec: ProblemSpec, seed: int) -> dict:
+    """Draw one utterance.
+
+    Returns a dict with the boundary inputs
+      x   complex64  [I, J, M]   observed STFT
+      a   complex128 [I, M]      target steering vector (back-projected)
+      Rp  complex128 [I, M, M]   rank-(M-1) noise SCM R'
+      rh0 float32    [I, J]      initial target variance
+      ru0 float32    [I, J]      initial noise variance
+    and the ground truth  a_true, h_true (complex64 [I, J, M], target image),
+    rh_true, ru_true, W (perturbed demixing matrices, complex128 [I, M, M]).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    M, I, J, K = spec.M, spec.I, spec.J, spec.K
+    f = np.arange(I) * FS / spec.nfft                       # [I]
+
+    pos = _mic_positions(spec)                               # [M, 2]
+    if spec.geometry == "linear":
+        theta = rng.uniform(0.0, np.pi)
+    else:
+        theta = rng.uniform(0.0, 2.0 * np.pi)
+    direction = np.array([np.cos(theta), np.sin(theta)])
+    delay = -(pos @ direction) / C_SOUND                     # [M]
+    a_true = np.exp(-2j * np.pi * f[:, None] * delay[None, :]) / np.sqrt(M)
+
+    dist = np.linalg.norm(pos[:, None, :] - pos[None, :, :], axis=-1)  # [M, M]
+    # np.sinc(v) = sin(pi v)/(pi v); the coherence is sin(z)/z, z = 2 pi f d / c
+    R_true = np.sinc(2.0 * f[:, None, None] * dist[None] / C_SOUND) + 1e-3 * np.eye(M)
+    L_true = np.linalg.cholesky(R_true)                      # [I, M, M]
+
+    T = rng.gamma(1.0, 1.0, size=(I, K))
+    V = rng.gamma(1.0, 1.0, size=(K, J))
+    rh_true = T @ V                                          # [I, J]
+    ru_true = rng.gamma(2.0, 0.5, size=(I, J))
+
+    s = np.sqrt(rh_true / 2.0) * (rng.standard_normal((I, J)) + 1j * rng.standard_normal((I, J)))
+    nse = (rng.standard_normal((I, J, M)) + 1j * rng.standard_normal((I, J, M))) / np.sqrt(2.0)
+    u = np.sqrt(ru_true)[..., None] * np.einsum("imn,ijn->ijm", L_true, nse)
+    h_true = a_true[:, None, :] * s[..., None]
+    x = (h_true + u).astype(np.complex64)
+    xd = x.astype(np.complex128)
+
+    # ILRMA stand-in: W_true = Q^H with Q unitary and Q[:, 0] = a_true.
+    Z = rng.standard_normal((I, M, M)) + 1j * rng.standard_normal((I, M, M))
+    Z[:, :, 0] = a_true
+    Q, Rq = np.linalg.qr(Z)
+    ph = Rq[:, 0, 0] / np.abs(Rq[:, 0, 0])
+    Q[:, :, 0] *= ph[:, None]
+    W_true = np.conj(np.transpose(Q, (0, 2, 1)))
+    G = (rng.standard_normal((I, M, M)) + 1j * rng.standard_normal((I, M, M))) / np.sqrt(2.0)
+    W = W_true + 0.01 * (np.sqrt(M) / M) * G                # ||W_true||_F = sqrt(M)
+    Winv = np.linalg.inv(W)
+    a = Winv[:, :, 0].copy()                                 # back-projected target column
+
+    # Eq. (eq:rit): back-projection of the M-1 noise outputs, averaged over j.
+    y = np.einsum("imn,ijn->ijm", W, xd)                     # y_n = w_n^H x
+    p = np.mean(np.abs(y) ** 2, axis=1)                      # [I, M]
+    p[:, 0] = 0.0
+    Rp = np.einsum("imk,ik,ink->imn", Winv, p, np.conj(Winv))
+    Rp = 0.5 * (Rp + np.conj(np.transpose(Rp, (0, 2, 1))))
+
+    # Eq. (eq:ruinit): r_u = y_u^H R'^+ y_u / M with the back-projected noise image.
+    y[:, :, 0] = 0.0
+    yu = np.einsum("imn,ijn->ijm", Winv, y)
+    Rp_pinv = np.linalg.pinv(Rp, hermitian=True, rcond=1e-10)
+    ru0 = np.real(np.einsum("ijm,imn,ijn->ij", np.conj(yu), Rp_pinv, yu)) / M
+    ru0 = np.maximum(ru0, 1e-6 * np.mean(ru0))
+
+    # Eq. (eq:rhinit) stand-in: the true NMF factors with 1 % multiplicative noise.
+    That = T * np.maximum(1.0 + 0.01 * rng.standard_normal(T.shape), 1e-3)
+    Vhat = V * np.maximum(1.0 + 0.01 * rng.standard_normal(V.shape), 1e-3)
+    rh0 = That @ Vhat
+
+    return dict(
+        x=x, a=a, Rp=Rp,
+        rh0=rh0.astype(np.float32), ru0=ru0.astype(np.float32),
+        a_true=a_true, h_true=h_true.astype(np.complex64),
+        rh_true=rh_true, ru_true=ru_true, W=W, spec=spec, seed=seed,
+    )
+
+
+# --------------------------------------------------------------------------
+# Named workloads (sizes of the paper's STFT scale; Table II gives fs, alpha,
+# beta; the iteration counts and sizes below are the workloads measured here).
+# --------------------------------------------------------------------------
+
+def workload(name: str, n_utt: Optional[int] = None) -> Workload:
+    """Return a named workload.
+
+    plain-m2     M=2, I=257 (nfft 512), J=250, linear 4 cm, K=10, 50 iterations
+    single-m4    M=4, I=1025 (nfft 2048), J=1000, linear 3 cm, K=20, 100 iterations
+    batch-256    256 utterances, I=513, J ~ U[200, 2000], M in {2, 4, 6},
+                 linear 4 cm, K=10, 100 iterations
+    adjoint-16   16 utterances of M=4, I=513, J=500, linear 3 cm, K=10, 20 iterations
+    scale-m8     M=8 circular (radius 5 cm), I=2049 (nfft 4096), J=4000, K=10, 200 iterations
+    """
+    if name == "plain-m2":
+        specs = [ProblemSpec(M=2, I=257, J=250, K=10, spacing=0.04)]
+        return Workload(name, specs, 50, BASE_SEED + 0)
+    if name == "single-m4":
+        specs = [ProblemSpec(M=4, I=1025, J=1000, K=20, spacing=0.03)]
+        return Workload(name, specs, 100, BASE_SEED + 1)
+    if name == "batch-256":
+        n = 256 if n_utt is None else n_utt
+        rng = np.random.Generator(np.random.PCG64(BASE_SEED + 2))
+        Js = rng.integers(200, 2001, size=256)
+        Ms = rng.choice([2, 4, 6], size=256)
+        specs = [ProblemSpec(M=int(Ms[u]), I=513, J=int(Js[u]), K=10, spacing=0.04)
+                 for u in range(n)]
+        return Workload(name, specs, 100, BASE_SEED + 2)
+    if name == "adjoint-16":
+        n = 16 if n_utt is None else n_utt
+        specs = [ProblemSpec(M=4, I=513, J=500, K=10, spacing=0.03) for _ in range(n)]
+        return Workload(name, specs, 20, BASE_SEED + 3, extra={"ckpt_stride": 5})
+    if name == "scale-m8":
+        specs = [ProblemSpec(M=8, I=2049, J=4000, K=10, geometry="circular", spacing=0.05)]
+        return Workload(name, specs, 200, BASE_SEED + 4)
+    raise KeyError(name)
+
+
+def utterance_seed(wl: Workload, u: int) -> int:
+    """Seed of utterance u of a workload (independent PCG64 streams)."""
+    return int(np.random.SeedSequence([wl.seed, u]).generate_state(1, dtype=np.uint64)[0] >> 1)
+
+
+def make_workload(wl: Workload) -> List[dict]:
+    return [make_problem(s, utterance_seed(wl, u)) for u, s in enumerate(wl.specs)]
+
+
+def tiny(M: int = 3, I: int = 5, J: int = 7, K: int = 3, seed: int = 7, **kw) -> dict:
+    """A tiny problem for brute-force checks."""
+    return make_problem(ProblemSpec(M=M, I=I, J=J, K=K, **kw), seed)
