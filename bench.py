@@ -1,0 +1,437 @@
+#!/usr/bin/env python
+"""Throughput benchmark of rank-constrained SCM estimation on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload single-m4|plain-m2|batch-256|scale-m8] [--rule accel|naive]
+                    [--iters-per-launch k]
+
+A step is one pass of the whole hot path over one workload with inputs resident
+in HBM: per-frequency setup and per-slot invariants, n_iter EM passes, Wiener
+extraction.  The metric is EM TF-slot updates per second (sum I*J*n_iter / step
+time).  L2 is flushed (a 256 MB write) between timed steps, outside the per-step
+CUDA-event brackets.  One JSON line is printed by rank 0.
+
+--impl reference times the FP64 CPU oracle (the paper's algorithm as plain
+numpy) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EM TF-slot updates/s (I·J·iter/s) accel vs naive at M=4; % of HBM roofline"
+UNIT = "slot-updates/s"
+DATA = "synthetic: seeded plane-wave target + spherically isotropic diffuse noise (stands in for JNAS speech + measured RIRs)"
+# FP32-pipe operations of one slot update of the accelerated kernel (FFMA, FMUL,
+# FMNMX, each one lane-op), counted from csrc/iterate.cu; plus 2 MUFU reciprocals.
+ACCEL_FP32_OPS_PER_SLOT_ITER = 27
+# Algorithmic bytes per slot of one accelerated launch: read tau_ax, sigma_bx
+# (16 B), kappa (4 B), r_h, r_u (8 B); write r_h, r_u (8 B).
+ACCEL_BYTES_PER_SLOT_LAUNCH = 36
+GB300_SMS = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="single-m4")
+    ap.add_argument("--rule", choices=["accel", "naive"], default="accel")
+    ap.add_argument("--iters-per-launch", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--naive-steps", type=int, default=None, help="timed naive steps (default min(steps, 10))")
+    ap.add_argument("--no-naive", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--clock-preroll", type=float, default=1.5, help="seconds of load before the timed region")
+    ap.add_argument("--json-out", default=None)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the GPU works."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.marks = {}
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(gpu_index), "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                self.samples.append((time.perf_counter(), float(parts[0]), float(parts[1]), parts[2], parts[3:7]))
+            except ValueError:
+                pass
+
+    def wait_first(self, timeout=5.0):
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.samples and time.perf_counter() - t0 < timeout:
+            time.sleep(0.02)
+
+    def mark(self, name):
+        self.marks[name] = time.perf_counter()
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        t0, t1 = self.marks.get("timed_start", 0), self.marks.get("timed_end", 1e30)
+        p0 = self.marks.get("preroll_start", t0)
+        timed = [s for s in self.samples if t0 <= s[0] <= t1]
+        window = timed if len(timed) >= 3 else [s for s in self.samples if p0 <= s[0] <= t1]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in window for k, v in enumerate(s[4]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(s[1] for s in window) if window else None,
+                "sm_max_mhz": max(s[2] for s in window) if window else None,
+                "reasons": reasons, "samples": len(window), "samples_in_timed_region": len(timed),
+                "window": "timed region" if window is timed else "pre-roll load + timed region"}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def make_inputs(name):
+    from paper_1908_01964_gb300 import synth
+    wl = synth.workload(name)
+    return wl, synth.make_workload(wl)
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The FP64 numpy oracle on the host cores (bounded sample of the workload)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    from oracle import rcscm_oracle as O
+    wl, probs = make_inputs(args.workload)
+    p = probs[0]
+    rows = choose_sample_rows(p, wl.n_iter, target_s=max(0.5, min(10.0, 150.0 / max(1, args.steps + args.warmup))))
+    J = p["x"].shape[1]
+    times, cpu = [], []
+    for k in range(args.warmup + args.steps):
+        c0, t0 = time.process_time(), time.perf_counter()
+        O.run(p, wl.n_iter, "accel2" if args.rule == "accel" else "naive", rows=rows)
+        dt, dc = time.perf_counter() - t0, time.process_time() - c0
+        if k >= args.warmup:
+            times.append(dt)
+            cpu.append(dc)
+    units = len(rows) * J * wl.n_iter
+    ms = 1e3 * statistics.mean(times)
+    value = units / (ms / 1e3)
+    cores = max(1, round(sum(cpu) / sum(times)))
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": DATA, "impl": "reference",
+        "config": {"workload": wl.name, "rule": args.rule, "n_iter": wl.n_iter,
+                   "sample": f"{len(rows)} of {p['x'].shape[0]} frequency rows (rows are independent)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{len(rows)} rows x J={J} x {wl.n_iter} iterations of {wl.name}, "
+                                   f"setup + invariants + iterations + Wiener, numpy FP64"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def choose_sample_rows(p, n_iter, target_s):
+    """Rows of one utterance whose oracle run takes about target_s seconds."""
+    from oracle import rcscm_oracle as O
+    I = p["x"].shape[0]
+    probe = np.arange(min(8, I))
+    t0 = time.perf_counter()
+    O.run(p, n_iter, "accel2", rows=probe)
+    per_row = (time.perf_counter() - t0) / len(probe)
+    n = int(min(I, max(len(probe), target_s / max(per_row, 1e-6))))
+    return np.linspace(0, I - 1, n).round().astype(int)
+
+
+def cpu_baseline(p, wl, rule):
+    from oracle import rcscm_oracle as O
+    rows = choose_sample_rows(p, wl.n_iter, target_s=15.0)
+    c0, t0 = time.process_time(), time.perf_counter()
+    O.run(p, wl.n_iter, "accel2" if rule == "accel" else "naive", rows=rows)
+    dt, dc = time.perf_counter() - t0, time.process_time() - c0
+    J = p["x"].shape[1]
+    return {"value": len(rows) * J * wl.n_iter / dt, "unit": UNIT, "cores": max(1, round(dc / dt)), "kind": "oracle",
+            "sample": f"{len(rows)} of {p['x'].shape[0]} rows x J={J} x {wl.n_iter} iterations of {wl.name} "
+                      f"(setup + invariants + iterations + Wiener), numpy FP64, {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def time_steps(solver, h, n_iter, K, W, flush, stream, sampler=None, preroll_s=0.0):
+    import torch
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def one(record):
+        flush.zero_()
+        e = [ev() for _ in range(4)] if record else None
+        if record:
+            e[0].record(stream)
+        solver.setup()
+        if record:
+            e[1].record(stream)
+        solver.iterate(n_iter)
+        if record:
+            e[2].record(stream)
+        solver.extract(out=h)
+        if record:
+            e[3].record(stream)
+        return e
+
+    for _ in range(W):
+        one(False)
+    if sampler is not None:
+        sampler.mark("preroll_start")
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < preroll_s:
+            for _ in range(8):
+                one(False)
+            torch.cuda.synchronize()
+    return one
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1908_01964_gb300 import build as B
+    from paper_1908_01964_gb300 import rcscm as R
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    B.build()
+    R.lib()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl, probs = make_inputs(args.workload)
+    n_iter = wl.n_iter
+    slots = wl.slots
+    dprobs = [R.to_device(p, dev) for p in probs]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    peaks = load_peaks()
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    # ---------------- accelerated (or chosen) rule: the headline
+    solver = R.Solver(dprobs, rule=args.rule, iters_per_launch=args.iters_per_launch, block=args.block)
+    h = torch.empty(solver.out_elements, dtype=torch.complex64, device=dev)
+    sampler = ClockSampler(torch.cuda.current_device() if ws == 1 else local) if rank == 0 or ws == 1 else None
+    if sampler:
+        sampler.wait_first()
+    one = time_steps(solver, h, n_iter, args.steps, args.warmup, flush, stream, sampler, args.clock_preroll)
+    barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark("timed_start")
+    events = [one(True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    barrier()
+    if sampler:
+        sampler.mark("timed_end")
+        sampler.stop()
+    code = solver.status()
+    if code not in (R.OK, R.ECLAMP):
+        raise RuntimeError(f"device status after the timed steps: {R.strerror(code)}")
+    step_ms = [e[0].elapsed_time(e[3]) for e in events]
+    seg = {k: [e[i].elapsed_time(e[i + 1]) for e in events] for i, k in enumerate(("setup", "iterate", "extract"))}
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * slots * n_iter / (ms_per_step / 1e3)
+    it_ms = statistics.mean(seg["iterate"])
+    launches_per_iterate = 1 if args.iters_per_launch == 0 else -(-n_iter // args.iters_per_launch)
+    launch_ms = it_ms / launches_per_iterate
+    iters_per_launch = n_iter if args.iters_per_launch == 0 else args.iters_per_launch
+
+    clocks = sampler.summary() if sampler else None
+    if args.rule == "accel" and args.iters_per_launch == 0:
+        ops = ACCEL_FP32_OPS_PER_SLOT_ITER * slots * iters_per_launch
+        achieved = ops / (launch_ms / 1e3) / 1e9
+        peak = GB300_SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (FP32 lane-ops)",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz max SM clock",
+                    "kernel": "accel_kernel (register-resident, all iterations in one launch)",
+                    "algorithmic": f"{ACCEL_FP32_OPS_PER_SLOT_ITER} FP32 ops + 2 MUFU per slot-iteration",
+                    "hbm_gbs_algorithmic": ACCEL_BYTES_PER_SLOT_LAUNCH * slots / (launch_ms / 1e3) / 1e9}
+    elif args.rule == "accel":
+        bytes_ = ACCEL_BYTES_PER_SLOT_LAUNCH * slots
+        achieved = bytes_ / (launch_ms / 1e3) / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
+                    "kernel": f"accel_kernel (streaming, {iters_per_launch} iteration(s) per launch)",
+                    "algorithmic": f"{ACCEL_BYTES_PER_SLOT_LAUNCH} B per slot per launch"}
+    else:
+        roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
+                    "kernel": "naive_kernel"}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": DATA, "impl": "ours",
+        "config": {"workload": wl.name, "utterances": len(probs), "slots": slots, "n_iter": n_iter,
+                   "M": sorted({s.M for s in wl.specs}), "I": sorted({s.I for s in wl.specs}),
+                   "J": [min(s.J for s in wl.specs), max(s.J for s in wl.specs)], "rule": args.rule,
+                   "iters_per_launch": args.iters_per_launch, "block": args.block,
+                   "step": "setup + invariants + n_iter EM passes + Wiener extraction, inputs resident in HBM",
+                   "l2": "flushed between timed steps (256 MB write outside the step's event brackets)",
+                   "parallelism": f"replicas x{ws} (one utterance set per GPU, no collective)"},
+        "kernels_ms": {k: statistics.mean(v) for k, v in seg.items()},
+        "roofline": roofline,
+        "gpu_launches": args.steps * (2 + launches_per_iterate + 1),
+        "clocks": clocks,
+    }
+
+    # ---------------- naive rule on the same workload (accel vs naive at M=4)
+    if not args.no_naive and args.rule == "accel":
+        kn = args.naive_steps if args.naive_steps is not None else min(args.steps, 10)
+        for key, rule, k_steps in (("naive", "naive", kn), ("naive_f64", "naive64", max(1, min(kn, 3)))):
+            nsolver = R.Solver(dprobs, rule=rule)
+            none = time_steps(nsolver, h, n_iter, k_steps, 1, flush, stream)
+            barrier()
+            torch.cuda.synchronize()
+            nev = [none(True) for _ in range(k_steps)]
+            torch.cuda.synchronize()
+            ncode = nsolver.status()
+            n_ms = statistics.mean(e[0].elapsed_time(e[3]) for e in nev)
+            n_it = statistics.mean(e[1].elapsed_time(e[2]) for e in nev)
+            nsolver.close()
+            result[key] = {"value": slots * n_iter / (n_ms / 1e3), "ms_per_step": n_ms, "iterate_ms": n_it,
+                           "steps": k_steps, "arithmetic": "f64" if rule == "naive64" else "f32",
+                           "status": R.strerror(ncode),
+                           "speedup_accel_over_naive_step": n_ms / ms_per_step,
+                           "speedup_accel_over_naive_iterate": n_it / it_ms}
+        result["naive"]["paper"] = ("87x: second-stage vs naive per iteration, MATLAB R2019a FP64 on an "
+                                    "Intel Core i9-7900X, M=4, I=513, J~275")
+
+    # ---------------- end to end through the C ABI with host buffers
+    if not args.no_e2e and len(probs) == 1:
+        result["e2e"] = e2e_host(probs[0], n_iter, args, R)
+    elif not args.no_e2e:
+        result["e2e"] = None
+
+    # ---------------- FP64 oracle on the host cores
+    if not args.no_cpu_baseline and rank == 0 and ws == 1:
+        result["cpu_baseline"] = cpu_baseline(probs[0], wl, args.rule)
+    solver.close()
+    return result if rank == 0 else None
+
+
+def e2e_host(p, n_iter, args, R):
+    """rcscm_solve_host from pinned host memory: H2D of the inputs, setup,
+    iterations, Wiener filter and D2H of h inside the timed region."""
+    import ctypes
+
+    import torch
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    x, a, Rp = pin(p["x"].astype(np.complex64)), pin(p["a"].astype(np.complex128)), pin(p["Rp"].astype(np.complex128))
+    rh0, ru0 = pin(p["rh0"].astype(np.float32)), pin(p["ru0"].astype(np.float32))
+    h = torch.empty(x.shape, dtype=torch.complex64).pin_memory()
+    I, J, M = x.shape
+    o = R.options(rule=args.rule, iters_per_launch=args.iters_per_launch, block=args.block)
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    L = R.lib()
+
+    def call():
+        return L.rcscm_solve_host(I, J, M, vp(x), vp(a), vp(Rp), None, vp(rh0), vp(ru0), ctypes.byref(o),
+                                  n_iter, vp(h), None, None, None)
+    for _ in range(2):
+        assert call() in (R.OK, R.ECLAMP)
+    k = max(3, min(args.steps, 10))
+    times = []
+    for _ in range(k):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        code = call()
+        times.append(time.perf_counter() - t0)
+        assert code in (R.OK, R.ECLAMP), R.strerror(code)
+    t = statistics.median(times)
+    h2d = sum(t_.numel() * t_.element_size() for t_ in (x, a, Rp, rh0, ru0))
+    return {"value": I * J * n_iter / t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": h.numel() * h.element_size(), "ms_per_step": 1e3 * t, "steps": k,
+            "api": "rcscm_solve_host (allocates, copies from pinned host memory, solves, copies h back; synchronous)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        res = run_reference(args)
+    else:
+        res = run_ours(args)
+    if res is not None:
+        line = json.dumps(res)
+        print(line, flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(line + "\n")
+    ws, _, _ = dist_env()
+    if ws > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * rcscm.h -- C ABI of the GB300 (sm_103a) library for rank-constrained spatial
+ * covariance matrix (SCM) estimation, Kubo, Takamune, Kitamura, Saruwatari,
+ * "Acceleration of rank-constrained spatial covariance matrix estimation for
+ * blind speech extraction", APSIPA 2019.
+ *
+ * Model (Sec. II-B-1): x_ij = h_ij + u_ij, h_ij = a_i s_ij with
+ * s_ij ~ N_c(0, r^(h)_ij), r^(h)_ij ~ IG(alpha, beta), and
+ * u_ij ~ N_c(0, r^(u)_ij R_i), R_i = R'_i + lambda_i b_i b_i^H, where R'_i is the
+ * rank-(M-1) noise SCM of Eq. (eq:rit) and b_i its unit null eigenvector.
+ * The library estimates r^(h), r^(u), lambda by EM (Sec. II-B-2) with either
+ * the second-stage accelerated rule (Algorithm 2, Sec. III-C-2) or the naive
+ * rule (per-slot M x M inverse, Sec. II-B-2), then extracts the target with the
+ * multichannel Wiener filter (Sec. II-A, Sec. IV-B).
+ *
+ * Conventions for every entry point:
+ *  - Indices: i frequency bin (I), j frame (J), m microphone (M, 2 <= M <= 8).
+ *  - "device" pointers are CUDA global-memory addresses on the current device;
+ *    "host" pointers are ordinary CPU memory.  Complex numbers are interleaved
+ *    (re, im) pairs: complex64 = 2 x float, complex128 = 2 x double.  All arrays
+ *    are dense, row-major, without padding, in the index order given.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued on it; calls return without synchronising unless stated.
+ *  - The caller owns every buffer it passes.  A context owns its derived data
+ *    (per-frequency constants, per-slot invariants, EM state, status word) and
+ *    frees it in rcscm_destroy.
+ *  - Every call returns an rcscm status code (RCSCM_OK = 0) and never aborts,
+ *    traps or prints.  Errors detected on the device are collected in a status
+ *    word that rcscm_status reads back.
+ */
+#ifndef RCSCM_H
+#define RCSCM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define RCSCM_OK          0
+#define RCSCM_EINVAL      1  /* bad shape, pointer, option or call order          */
+#define RCSCM_ENULLSPACE  2  /* R'_i is not rank M-1 within options.null_tol      */
+#define RCSCM_ENONFINITE  3  /* a NaN/Inf or non-positive lambda_i was produced   */
+#define RCSCM_ECLAMP      4  /* warning: some r^(u) reached options.ru_floor, or a
+                                naive-rule r^(h) estimate fell below zero in FP32 and
+                                was held at beta/(alpha+2)                         */
+#define RCSCM_ECUDA       5  /* a CUDA runtime call failed                         */
+#define RCSCM_ENOMEM      6  /* device allocation failed                           */
+#define RCSCM_ETIMEOUT    7  /* reserved: a bounded device wait gave up            */
+
+/* ---- update rules ------------------------------------------------------ */
+#define RCSCM_RULE_ACCEL  0  /* second-stage accelerated rule, Algorithm 2         */
+#define RCSCM_RULE_NAIVE  1  /* naive rule, Eqs. (eq:rijx)-(eq:M_ru), FP32 arithmetic */
+#define RCSCM_RULE_NAIVE_F64 2 /* naive rule in FP64 arithmetic (state kept in FP32)  */
+
+#define RCSCM_MAX_M       8  /* largest supported number of microphones          */
+#define RCSCM_MAX_J_ACCEL 4096 /* longest row (frames) of the accelerated kernel  */
+
+typedef struct rcscm_ctx rcscm_ctx;
+
+/* One utterance.  All pointers are device pointers and must stay valid (and
+ * unchanged) from rcscm_create until rcscm_destroy; rcscm_setup reads x, a, Rp,
+ * lambda0, rh0, ru0, and the naive rule re-reads x at every iteration. */
+typedef struct {
+    int64_t I, J, M;
+    const void*   x;        /* complex64  [I][J][M]  observed STFT x_ij                 */
+    const void*   a;        /* complex128 [I][M]     steering vector a_i^(h)            */
+    const void*   Rp;       /* complex128 [I][M][M]  R'_i^(u), Hermitian, rank M-1      */
+    const double* lambda0;  /* [I] initial lambda_i, or NULL: the smallest nonzero
+                               eigenvalue of R'_i (Sec. II-B-3)                          */
+    const float*  rh0;      /* [I][J] initial r^(h)_ij (Eq. (eq:rhinit)), > 0            */
+    const float*  ru0;      /* [I][J] initial r^(u)_ij (Eq. (eq:ruinit)), > 0            */
+} rcscm_problem;
+
+typedef struct {
+    int    rule;             /* RCSCM_RULE_ACCEL (default), RCSCM_RULE_NAIVE or
+                                RCSCM_RULE_NAIVE_F64                                    */
+    double alpha;            /* inverse-gamma shape, Table II: 1.1                      */
+    double beta;             /* inverse-gamma scale, Table II: 1e-16                    */
+    float  ru_floor;         /* lower bound applied to r^(u) (default FLT_MIN)          */
+    double null_tol;         /* zero-eigenvalue test: mu_1 <= null_tol * mu_M (1e-6)   */
+    int    block;            /* threads per row of the accelerated kernel: 0 = choose
+                                by J, else 128, 256, 512 or 1024                         */
+    int    iters_per_launch; /* 0: every iteration of one rcscm_iterate call in one
+                                register-resident launch; k > 0: one launch per k
+                                iterations, state streamed through HBM between them    */
+} rcscm_options;
+
+/* Fill *opt with the defaults listed above. */
+void rcscm_default_options(rcscm_options* opt);
+
+/* Validate the shapes of n_probs utterances (uneven J and mixed M allowed),
+ * allocate the context's device memory and upload its row tables on `stream`.
+ * *ctx receives the new context (NULL on error).  No estimator work is done.
+ * Errors: EINVAL (NULL pointer, M outside [2, 8], I or J < 1, J above
+ * RCSCM_MAX_J_ACCEL for the accelerated rule, bad option), ENOMEM, ECUDA. */
+int rcscm_create(rcscm_ctx** ctx, const rcscm_problem* probs, int n_probs,
+                 const rcscm_options* opt, void* stream);
+
+/* Per-frequency setup and per-slot invariants, then EM state initialisation.
+ * Setup (FP64, Sec. II-B-1, Eq. (eq:riinv), (eq:taa), (eq:sap)): symmetrise R'_i,
+ * Hermitian eigendecomposition, b_i = eigenvector of the smallest eigenvalue,
+ * (R'_i)^+, lambda_i (Sec. II-B-3), tau^(aa)_i, sigma^(ab)_i.  Invariants (FP32,
+ * Algorithm 2 before its loop; Eq. (eq:tax), (eq:txx), (eq:spx)): tau^(ax)_ij,
+ * sigma^(bx)_ij and kappa_ij = tau^(xx)_ij - |tau^(ax)_ij|^2 / tau^(aa)_i >= 0.
+ * State: r^(h) <- rh0, r^(u) <- ru0, lambda <- lambda0.  May be called again to
+ * restart from the (possibly updated) input buffers.  A failed null-space test
+ * is reported by rcscm_status as RCSCM_ENULLSPACE. */
+int rcscm_setup(rcscm_ctx* ctx, void* stream);
+
+/* Run n_iter EM passes (n_iter >= 0) of the context's rule on every utterance.
+ * Accelerated rule: the repeat loop of Algorithm 2 (Sec. III-C-2) -- gamma~_ij
+ * (eq:tal), r^(h) (eq:1st_rh), lambda_i (eq:1st_li, a mean over j), r^(u)
+ * (eq:1st_ru with the new lambda_i).  Naive rule: E-step (eq:rijx)-(eq:E_hru)
+ * with an explicit M x M inverse per slot, then M-step (eq:M_rh)-(eq:M_ru); in
+ * FP32 its r_h estimate and b^H R^u b, non-negative in exact arithmetic, are held
+ * at zero when rounding makes them negative (reported as RCSCM_ECLAMP). */
+int rcscm_iterate(rcscm_ctx* ctx, int n_iter, void* stream);
+
+/* Multichannel Wiener filter with the current state: the posterior mean
+ * h_ij = r^(h) a a^H (R^(x)_ij)^{-1} x_ij = [r^(h) rho^(ax) / (r^(u) + r^(h) rho^(aa))] a_i.
+ * h_out: device complex64, the utterances concatenated in order, each [I][J][M]. */
+int rcscm_extract(rcscm_ctx* ctx, void* h_out, void* stream);
+
+/* Copy one utterance's state out of / into the context (device pointers:
+ * rh, ru [I][J] float, lambda [I] float).  set_state accepts any of them NULL
+ * (left unchanged).  Errors: EINVAL for a bad index. */
+int rcscm_get_state(rcscm_ctx* ctx, int prob, float* rh, float* ru, float* lambda, void* stream);
+int rcscm_set_state(rcscm_ctx* ctx, int prob, const float* rh, const float* ru,
+                    const float* lambda, void* stream);
+
+/* Setup results of one utterance (device pointers, any may be NULL):
+ * b complex128 [I][M], lambda0 double [I], tau_aa double [I],
+ * sigma_ab complex128 [I], mu double [I][M] (ascending eigenvalues of R'_i). */
+int rcscm_get_setup(rcscm_ctx* ctx, int prob, void* b, double* lambda0, double* tau_aa,
+                    void* sigma_ab, double* mu, void* stream);
+
+/* Per-slot invariants of one utterance (device pointers, any may be NULL):
+ * tau_ax complex64 [I][J], sigma_bx complex64 [I][J], kappa float [I][J]. */
+int rcscm_get_invariants(rcscm_ctx* ctx, int prob, void* tau_ax, void* sigma_bx,
+                         float* kappa, void* stream);
+
+/* Synchronise `stream`, read and clear the device status word.  Returns the most
+ * severe code seen since the last call (ENULLSPACE, ENONFINITE, then ECLAMP);
+ * *flags (may be NULL) receives the raw bit set (bit k-1 for code k). */
+int rcscm_status(rcscm_ctx* ctx, int* flags, void* stream);
+
+/* Sizes: rows (sum of I), slots (sum of I*J), device bytes held by the context. */
+int rcscm_info(const rcscm_ctx* ctx, int64_t* rows, int64_t* slots, int64_t* device_bytes);
+
+/* Free the context (synchronises the device first).  NULL is accepted. */
+void rcscm_destroy(rcscm_ctx* ctx);
+
+/* Static, NUL-terminated description of a status code. */
+const char* rcscm_strerror(int code);
+
+/* One-shot solve of a single utterance from HOST memory: copies x, a, Rp, rh0,
+ * ru0 (same layouts as rcscm_problem, host pointers; lambda0 may be NULL) to the
+ * device, runs setup, n_iter passes and the Wiener filter, and copies h_out
+ * (complex64 [I][J][M]) and, when not NULL, rh, ru [I][J] and lambda [I] back to
+ * host memory.  Allocates and frees its own device buffers; synchronous. */
+int rcscm_solve_host(int64_t I, int64_t J, int64_t M, const void* x, const void* a,
+                     const void* Rp, const double* lambda0, const float* rh0,
+                     const float* ru0, const rcscm_options* opt, int n_iter,
+                     void* h_out, float* rh, float* ru, float* lambda);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCSCM_H */

@@ -142,12 +142,20 @@ def iterate_accel1(rh, ru, lam, x, a, st: Setup, alpha, beta):
     return rh_new, ru_new, lam_new
 
 
-def e_step_naive(rh_t, ru_t, lam_t, x, a, st: Setup):
+def e_step_naive(rh_t, ru_t, lam_t, x, a, st: Setup, dtype=np.complex128):
     """E-step of Sec. II-B-2 with an explicit M x M inverse per slot.
 
     Returns (rhat_h [I, J], Rhat_u [I, J, M, M]).  Eqs. (eq:rijx), (eq:E_hrh), (eq:E_hru).
+    ``dtype`` is the precision of the arithmetic: complex128 for the oracle;
+    the tests also evaluate the same formulas in complex64 to measure the
+    accuracy that single precision allows for this rule.
     """
-    x = np.asarray(x, np.complex128)
+    rdt = np.float32 if dtype == np.complex64 else np.float64
+    x = np.asarray(x, dtype)
+    a = np.asarray(a, dtype)
+    rh_t, ru_t, lam_t = (np.asarray(v, rdt) for v in (rh_t, ru_t, lam_t))
+    st = Setup(Rp=np.asarray(st.Rp, dtype), mu=st.mu, b=np.asarray(st.b, dtype), Rp_pinv=st.Rp_pinv,
+               lam0=st.lam0, tau_aa=st.tau_aa, sigma_ab=st.sigma_ab)
     bbH = np.einsum("im,in->imn", st.b, np.conj(st.b))
     Rt = st.Rp + lam_t[:, None, None] * bbH                                     # R~_i
     aaH = np.einsum("im,in->imn", a, np.conj(a))
@@ -165,8 +173,12 @@ def e_step_naive(rh_t, ru_t, lam_t, x, a, st: Setup):
     return rhat_h, Rhat_u
 
 
-def m_step_naive(rhat_h, Rhat_u, ru_t, st: Setup, M, alpha, beta):
+def m_step_naive(rhat_h, Rhat_u, ru_t, st: Setup, M, alpha, beta, dtype=np.complex128):
     """M-step of Sec. II-B-2: Eqs. (eq:M_rh), (eq:M_li), R_i update, (eq:M_ru)."""
+    rdt = np.float32 if dtype == np.complex64 else np.float64
+    ru_t, alpha, beta = np.asarray(ru_t, rdt), rdt(alpha), rdt(beta)
+    st = Setup(Rp=np.asarray(st.Rp, dtype), mu=st.mu, b=np.asarray(st.b, dtype), Rp_pinv=st.Rp_pinv,
+               lam0=st.lam0, tau_aa=st.tau_aa, sigma_ab=st.sigma_ab)
     rh_new = (rhat_h + beta) / (alpha + 2.0)                                     # (eq:M_rh)
     bRb = np.real(np.einsum("im,ijmn,in->ij", np.conj(st.b), Rhat_u, st.b))
     lam_new = np.mean(bRb / ru_t, axis=1)                                        # (eq:M_li)
@@ -177,18 +189,19 @@ def m_step_naive(rhat_h, Rhat_u, ru_t, st: Setup, M, alpha, beta):
     return rh_new, ru_new, lam_new
 
 
-def iterate_naive(rh, ru, lam, x, a, st: Setup, alpha, beta):
+def iterate_naive(rh, ru, lam, x, a, st: Setup, alpha, beta, dtype=np.complex128):
     """One EM pass of the naive rule (Sec. II-B-2), frequency by frequency."""
     M = np.asarray(x).shape[-1]
-    out_rh = np.empty_like(rh)
-    out_ru = np.empty_like(ru)
-    out_lam = np.empty_like(lam)
+    rdt = np.float32 if dtype == np.complex64 else np.float64
+    out_rh = np.empty(np.shape(rh), rdt)
+    out_ru = np.empty(np.shape(ru), rdt)
+    out_lam = np.empty(np.shape(lam), rdt)
     for i in range(rh.shape[0]):
         sub = Setup(Rp=st.Rp[i:i + 1], mu=st.mu[i:i + 1], b=st.b[i:i + 1],
                     Rp_pinv=st.Rp_pinv[i:i + 1], lam0=st.lam0[i:i + 1],
                     tau_aa=st.tau_aa[i:i + 1], sigma_ab=st.sigma_ab[i:i + 1])
-        rhat_h, Rhat_u = e_step_naive(rh[i:i + 1], ru[i:i + 1], lam[i:i + 1], x[i:i + 1], a[i:i + 1], sub)
-        r1, r2, l = m_step_naive(rhat_h, Rhat_u, ru[i:i + 1], sub, M, alpha, beta)
+        rhat_h, Rhat_u = e_step_naive(rh[i:i + 1], ru[i:i + 1], lam[i:i + 1], x[i:i + 1], a[i:i + 1], sub, dtype)
+        r1, r2, l = m_step_naive(rhat_h, Rhat_u, ru[i:i + 1], sub, M, alpha, beta, dtype)
         out_rh[i], out_ru[i], out_lam[i] = r1[0], r2[0], l[0]
     return out_rh, out_ru, out_lam
 

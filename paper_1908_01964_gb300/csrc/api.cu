@@ -1,0 +1,420 @@
+// C ABI of the rank-constrained SCM library (declarations and contracts in
+// include/rcscm.h).  Host code: validation, context memory, row tables and
+// kernel launches.  Every numerical step runs in the CUDA kernels of setup.cu,
+// iterate.cu and extract.cu.
+#include <float.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "rcscm_internal.cuh"
+
+using namespace rcscm;
+
+struct rcscm_ctx {
+    rcscm_options opt;
+    std::vector<rcscm_problem> probs;
+    std::vector<int64_t> row0, slot0, out0;   // per utterance: first row, slot, output element
+    int64_t R = 0, S = 0;
+    int n_blocks = 0;
+    int max_j = 0;
+    DevState d;
+    int* naive_rows = nullptr;
+    int count_by_m[kMaxM + 1];
+    int first_by_m[kMaxM + 1];
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+};
+
+namespace {
+
+int map_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return RCSCM_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return RCSCM_ENOMEM;
+    }
+    return RCSCM_ECUDA;
+}
+
+template <class T>
+int dalloc(rcscm_ctx* c, T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+    if (e != cudaSuccess) return map_cuda(e);
+    c->allocs.push_back(q);
+    c->bytes += (int64_t)(n * sizeof(T));
+    *p = static_cast<T*>(q);
+    return RCSCM_OK;
+}
+
+void free_all(rcscm_ctx* c) {
+    for (void* q : c->allocs) cudaFree(q);
+    c->allocs.clear();
+}
+
+int valid_options(const rcscm_options* o) {
+    if (o->rule != RCSCM_RULE_ACCEL && o->rule != RCSCM_RULE_NAIVE && o->rule != RCSCM_RULE_NAIVE_F64) return 0;
+    if (!(o->alpha > -2.0) || !(o->beta >= 0.0)) return 0;
+    if (!(o->null_tol > 0.0) || !(o->ru_floor >= 0.0f)) return 0;
+    if (o->block != 0 && o->block != 128 && o->block != 256 && o->block != 512 && o->block != 1024) return 0;
+    if (o->iters_per_launch < 0) return 0;
+    return 1;
+}
+
+IterParams iter_params(const rcscm_options& o) {
+    IterParams p;
+    p.c_a2 = (float)(1.0 / (o.alpha + 2.0));
+    p.c_b = (float)(o.beta / (o.alpha + 2.0));
+    p.ru_floor = o.ru_floor;
+    p.c_a2_f64 = 1.0 / (o.alpha + 2.0);
+    p.c_b_f64 = o.beta / (o.alpha + 2.0);
+    return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rcscm_default_options(rcscm_options* opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->rule = RCSCM_RULE_ACCEL;
+    opt->alpha = 1.1;
+    opt->beta = 1e-16;
+    opt->ru_floor = FLT_MIN;
+    opt->null_tol = 1e-6;
+    opt->block = 0;
+    opt->iters_per_launch = 0;
+}
+
+const char* rcscm_strerror(int code) {
+    switch (code) {
+        case RCSCM_OK: return "success";
+        case RCSCM_EINVAL: return "invalid argument (shape, pointer, option or call order)";
+        case RCSCM_ENULLSPACE: return "R' is not rank M-1 within the null-space tolerance (or a lies in its null space)";
+        case RCSCM_ENONFINITE: return "non-finite or non-positive lambda produced";
+        case RCSCM_ECLAMP: return "warning: a variance was held at its floor (r_u at ru_floor, or a negative FP32 naive-rule r_h estimate)";
+        case RCSCM_ECUDA: return "CUDA runtime error";
+        case RCSCM_ENOMEM: return "device memory allocation failed";
+        case RCSCM_ETIMEOUT: return "bounded device wait gave up";
+        default: return "unknown rcscm status code";
+    }
+}
+
+int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const rcscm_options* opt,
+                 void* stream) {
+    if (!out) return RCSCM_EINVAL;
+    *out = nullptr;
+    if (!probs || n_probs < 1 || !opt || !valid_options(opt)) return RCSCM_EINVAL;
+    const int max_block = opt->block ? opt->block : 512;
+    const int max_spt = (max_block == 1024) ? 4 : 8;
+    int64_t R = 0, S = 0, n_blocks = 0, naive_scratch = 0;
+    int max_j = 0;
+    for (int p = 0; p < n_probs; ++p) {
+        const rcscm_problem& q = probs[p];
+        if (q.I < 1 || q.J < 1 || q.M < 2 || q.M > kMaxM) return RCSCM_EINVAL;
+        if (!q.x || !q.a || !q.Rp || !q.rh0 || !q.ru0) return RCSCM_EINVAL;
+        if (q.J > INT32_MAX / 2) return RCSCM_EINVAL;
+        if (opt->rule == RCSCM_RULE_ACCEL && q.J > (int64_t)max_block * max_spt) return RCSCM_EINVAL;
+        R += q.I;
+        S += q.I * q.J;
+        n_blocks += q.I * ((q.J + kSlotBlock - 1) / kSlotBlock);
+        naive_scratch += q.I * q.J * q.M * q.M;
+        max_j = std::max<int>(max_j, (int)q.J);
+    }
+    if (R > INT32_MAX || n_blocks > INT32_MAX) return RCSCM_EINVAL;
+
+    rcscm_ctx* c = new (std::nothrow) rcscm_ctx();
+    if (!c) return RCSCM_ENOMEM;
+    c->opt = *opt;
+    c->probs.assign(probs, probs + n_probs);
+    c->R = R;
+    c->S = S;
+    c->n_blocks = (int)n_blocks;
+    c->max_j = max_j;
+
+    // ---- host row tables ----------------------------------------------------
+    std::vector<RowDesc> rows((size_t)R);
+    std::vector<BlockMap> bmap((size_t)n_blocks);
+    std::vector<int> jrow((size_t)R), mrow((size_t)R);
+    int64_t r = 0, s = 0, o = 0, sc = 0, b = 0;
+    for (int p = 0; p < n_probs; ++p) {
+        const rcscm_problem& q = probs[p];
+        c->row0.push_back(r);
+        c->slot0.push_back(s);
+        c->out0.push_back(o);
+        for (int64_t i = 0; i < q.I; ++i, ++r) {
+            RowDesc& rd = rows[(size_t)r];
+            rd.slot_off = s;
+            rd.out_off = o;
+            rd.scratch_off = sc;
+            rd.x = static_cast<const float2*>(q.x) + i * q.J * q.M;
+            rd.a = static_cast<const double2*>(q.a) + i * q.M;
+            rd.Rp = static_cast<const double2*>(q.Rp) + i * q.M * q.M;
+            rd.lambda0 = q.lambda0 ? q.lambda0 + i : nullptr;
+            rd.rh0 = q.rh0 + i * q.J;
+            rd.ru0 = q.ru0 + i * q.J;
+            rd.J = (int)q.J;
+            rd.M = (int)q.M;
+            rd.prob = p;
+            rd.freq = (int)i;
+            jrow[(size_t)r] = (int)q.J;
+            mrow[(size_t)r] = (int)q.M;
+            for (int j0 = 0; j0 < q.J; j0 += kSlotBlock) bmap[(size_t)b++] = BlockMap{(int)r, j0};
+            s += q.J;
+            o += q.J * q.M;
+            sc += q.J * q.M * q.M;
+        }
+    }
+    std::vector<int> order((size_t)R);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return jrow[(size_t)x] > jrow[(size_t)y]; });
+    std::vector<int> naive_rows;
+    naive_rows.reserve((size_t)R);
+    for (int M = 0; M <= kMaxM; ++M) {
+        c->first_by_m[M] = (int)naive_rows.size();
+        for (int64_t k = 0; k < R; ++k)
+            if (mrow[(size_t)order[(size_t)k]] == M) naive_rows.push_back(order[(size_t)k]);
+        c->count_by_m[M] = (int)naive_rows.size() - c->first_by_m[M];
+    }
+
+    // ---- device memory -------------------------------------------------------
+    DevState& d = c->d;
+    int st = RCSCM_OK;
+    const size_t Rz = (size_t)R, Sz = (size_t)S;
+    if (!st) st = dalloc(c, &d.rows, Rz);
+    if (!st) st = dalloc(c, &d.rc, Rz);
+    if (!st) st = dalloc(c, &d.bmap, (size_t)n_blocks);
+    if (!st) st = dalloc(c, &d.order, Rz);
+    if (!st) st = dalloc(c, &d.b64, Rz * kMaxM);
+    if (!st) st = dalloc(c, &d.mu, Rz * kMaxM);
+    if (!st) st = dalloc(c, &d.lam0, Rz);
+    if (!st) st = dalloc(c, &d.taa64, Rz);
+    if (!st) st = dalloc(c, &d.sab64, Rz);
+    if (!st) st = dalloc(c, &d.phi, Rz * 64);
+    if (!st) st = dalloc(c, &d.a32, Rz * kMaxM);
+    if (!st) st = dalloc(c, &d.b32, Rz * kMaxM);
+    if (!st) st = dalloc(c, &d.rp32, Rz * 64);
+    if (!st) st = dalloc(c, &d.inv4, Sz);
+    if (!st) st = dalloc(c, &d.kap, Sz);
+    if (!st) st = dalloc(c, &d.rh, Sz);
+    if (!st) st = dalloc(c, &d.ru, Sz);
+    if (!st) st = dalloc(c, &d.lam, Rz);
+    if (!st) st = dalloc(c, &d.status, 1);
+    if (!st) st = dalloc(c, &c->naive_rows, Rz);
+    if (!st && opt->rule == RCSCM_RULE_NAIVE) {
+        float* q = nullptr;
+        st = dalloc(c, &q, (size_t)naive_scratch);
+        d.ru_hat = q;
+    } else if (!st && opt->rule == RCSCM_RULE_NAIVE_F64) {
+        double* q = nullptr;
+        st = dalloc(c, &q, (size_t)naive_scratch);
+        d.ru_hat = q;
+    }
+    if (st) {
+        free_all(c);
+        delete c;
+        return st;
+    }
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(d.rows, rows.data(), Rz * sizeof(RowDesc), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.bmap, bmap.data(), (size_t)n_blocks * sizeof(BlockMap), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.order, order.data(), Rz * sizeof(int), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->naive_rows, naive_rows.data(), Rz * sizeof(int), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.status, 0, sizeof(int), cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);    // host tables go out of scope
+    if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return map_cuda(e);
+    }
+    *out = c;
+    return RCSCM_OK;
+}
+
+int rcscm_setup(rcscm_ctx* c, void* stream) {
+    if (!c) return RCSCM_EINVAL;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_setup(c->d, (int)c->R, c->opt.null_tol, cs);
+    if (e == cudaSuccess) e = launch_invariants(c->d, c->n_blocks, cs);
+    return map_cuda(e);
+}
+
+int rcscm_iterate(rcscm_ctx* c, int n_iter, void* stream) {
+    if (!c || n_iter < 0) return RCSCM_EINVAL;
+    if (n_iter == 0) return RCSCM_OK;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    const IterParams p = iter_params(c->opt);
+    const int chunk = c->opt.iters_per_launch > 0 ? c->opt.iters_per_launch : n_iter;
+    for (int done = 0; done < n_iter; done += chunk) {
+        const int k = std::min(chunk, n_iter - done);
+        cudaError_t e;
+        if (c->opt.rule == RCSCM_RULE_ACCEL)
+            e = launch_accel(c->d, (int)c->R, c->max_j, c->opt.block, k, p, cs);
+        else
+            e = launch_naive(c->d, c->naive_rows, c->count_by_m, c->first_by_m, k, p,
+                             c->opt.rule == RCSCM_RULE_NAIVE_F64, cs);
+        if (e != cudaSuccess) return map_cuda(e);
+    }
+    return RCSCM_OK;
+}
+
+int rcscm_extract(rcscm_ctx* c, void* h_out, void* stream) {
+    if (!c || !h_out) return RCSCM_EINVAL;
+    return map_cuda(launch_extract(c->d, c->n_blocks, static_cast<float2*>(h_out),
+                                   static_cast<cudaStream_t>(stream)));
+}
+
+int rcscm_get_state(rcscm_ctx* c, int p, float* rh, float* ru, float* lambda, void* stream) {
+    if (!c || p < 0 || p >= (int)c->probs.size()) return RCSCM_EINVAL;
+    const rcscm_problem& q = c->probs[(size_t)p];
+    const size_t n = (size_t)(q.I * q.J);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (rh) e = cudaMemcpyAsync(rh, c->d.rh + c->slot0[(size_t)p], n * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+    if (ru && e == cudaSuccess) e = cudaMemcpyAsync(ru, c->d.ru + c->slot0[(size_t)p], n * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+    if (lambda && e == cudaSuccess)
+        e = cudaMemcpyAsync(lambda, c->d.lam + c->row0[(size_t)p], (size_t)q.I * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+    return map_cuda(e);
+}
+
+int rcscm_set_state(rcscm_ctx* c, int p, const float* rh, const float* ru, const float* lambda, void* stream) {
+    if (!c || p < 0 || p >= (int)c->probs.size()) return RCSCM_EINVAL;
+    const rcscm_problem& q = c->probs[(size_t)p];
+    const size_t n = (size_t)(q.I * q.J);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (rh) e = cudaMemcpyAsync(c->d.rh + c->slot0[(size_t)p], rh, n * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+    if (ru && e == cudaSuccess) e = cudaMemcpyAsync(c->d.ru + c->slot0[(size_t)p], ru, n * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+    if (lambda && e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d.lam + c->row0[(size_t)p], lambda, (size_t)q.I * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+    return map_cuda(e);
+}
+
+int rcscm_get_setup(rcscm_ctx* c, int p, void* b, double* lambda0, double* tau_aa, void* sigma_ab,
+                    double* mu, void* stream) {
+    if (!c || p < 0 || p >= (int)c->probs.size()) return RCSCM_EINVAL;
+    const rcscm_problem& q = c->probs[(size_t)p];
+    const size_t r0 = (size_t)c->row0[(size_t)p], I = (size_t)q.I, M = (size_t)q.M;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (b) e = cudaMemcpy2DAsync(b, M * sizeof(double2), c->d.b64 + r0 * kMaxM, kMaxM * sizeof(double2),
+                                 M * sizeof(double2), I, cudaMemcpyDeviceToDevice, cs);
+    if (mu && e == cudaSuccess)
+        e = cudaMemcpy2DAsync(mu, M * sizeof(double), c->d.mu + r0 * kMaxM, kMaxM * sizeof(double),
+                              M * sizeof(double), I, cudaMemcpyDeviceToDevice, cs);
+    if (lambda0 && e == cudaSuccess) e = cudaMemcpyAsync(lambda0, c->d.lam0 + r0, I * sizeof(double), cudaMemcpyDeviceToDevice, cs);
+    if (tau_aa && e == cudaSuccess) e = cudaMemcpyAsync(tau_aa, c->d.taa64 + r0, I * sizeof(double), cudaMemcpyDeviceToDevice, cs);
+    if (sigma_ab && e == cudaSuccess) e = cudaMemcpyAsync(sigma_ab, c->d.sab64 + r0, I * sizeof(double2), cudaMemcpyDeviceToDevice, cs);
+    return map_cuda(e);
+}
+
+int rcscm_get_invariants(rcscm_ctx* c, int p, void* tau_ax, void* sigma_bx, float* kappa, void* stream) {
+    if (!c || p < 0 || p >= (int)c->probs.size()) return RCSCM_EINVAL;
+    const rcscm_problem& q = c->probs[(size_t)p];
+    const size_t s0 = (size_t)c->slot0[(size_t)p], n = (size_t)(q.I * q.J);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    const char* base = reinterpret_cast<const char*>(c->d.inv4 + s0);
+    if (tau_ax) e = cudaMemcpy2DAsync(tau_ax, sizeof(float2), base, sizeof(float4), sizeof(float2), n, cudaMemcpyDeviceToDevice, cs);
+    if (sigma_bx && e == cudaSuccess)
+        e = cudaMemcpy2DAsync(sigma_bx, sizeof(float2), base + sizeof(float2), sizeof(float4), sizeof(float2), n,
+                              cudaMemcpyDeviceToDevice, cs);
+    if (kappa && e == cudaSuccess) e = cudaMemcpyAsync(kappa, c->d.kap + s0, n * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+    return map_cuda(e);
+}
+
+int rcscm_status(rcscm_ctx* c, int* flags, void* stream) {
+    if (!c) return RCSCM_EINVAL;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    int h = 0;
+    cudaError_t e = cudaStreamSynchronize(cs);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, c->d.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(c->d.status, 0, sizeof(int));
+    if (e != cudaSuccess) return map_cuda(e);
+    if (flags) *flags = h;
+    if (h & kFlagNullspace) return RCSCM_ENULLSPACE;
+    if (h & kFlagNonfinite) return RCSCM_ENONFINITE;
+    if (h & kFlagClamp) return RCSCM_ECLAMP;
+    return RCSCM_OK;
+}
+
+int rcscm_info(const rcscm_ctx* c, int64_t* rows, int64_t* slots, int64_t* device_bytes) {
+    if (!c) return RCSCM_EINVAL;
+    if (rows) *rows = c->R;
+    if (slots) *slots = c->S;
+    if (device_bytes) *device_bytes = c->bytes;
+    return RCSCM_OK;
+}
+
+void rcscm_destroy(rcscm_ctx* c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+}
+
+int rcscm_solve_host(int64_t I, int64_t J, int64_t M, const void* x, const void* a, const void* Rp,
+                     const double* lambda0, const float* rh0, const float* ru0, const rcscm_options* opt,
+                     int n_iter, void* h_out, float* rh, float* ru, float* lambda) {
+    if (!x || !a || !Rp || !rh0 || !ru0 || !h_out || !opt || n_iter < 0) return RCSCM_EINVAL;
+    if (I < 1 || J < 1 || M < 2 || M > kMaxM) return RCSCM_EINVAL;
+    const size_t nx = (size_t)(I * J * M), ns = (size_t)(I * J), ni = (size_t)I;
+    void *dx = nullptr, *da = nullptr, *dR = nullptr, *dh = nullptr;
+    double* dl = nullptr;
+    float *drh = nullptr, *dru = nullptr;
+    int st = RCSCM_OK;
+    cudaError_t e = cudaMalloc(&dx, nx * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&da, ni * (size_t)M * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&dR, ni * (size_t)(M * M) * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&dh, nx * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&drh, ns * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dru, ns * sizeof(float));
+    if (e == cudaSuccess && lambda0) e = cudaMalloc(&dl, ni * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(dx, x, nx * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(da, a, ni * (size_t)M * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dR, Rp, ni * (size_t)(M * M) * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(drh, rh0, ns * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dru, ru0, ns * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && lambda0) e = cudaMemcpy(dl, lambda0, ni * sizeof(double), cudaMemcpyHostToDevice);
+    st = map_cuda(e);
+    rcscm_ctx* c = nullptr;
+    if (!st) {
+        rcscm_problem q;
+        q.I = I; q.J = J; q.M = M;
+        q.x = dx; q.a = da; q.Rp = dR; q.lambda0 = dl; q.rh0 = drh; q.ru0 = dru;
+        st = rcscm_create(&c, &q, 1, opt, nullptr);
+    }
+    if (!st) st = rcscm_setup(c, nullptr);
+    if (!st) st = rcscm_iterate(c, n_iter, nullptr);
+    if (!st) st = rcscm_extract(c, dh, nullptr);
+    if (!st) st = map_cuda(cudaMemcpy(h_out, dh, nx * sizeof(float2), cudaMemcpyDeviceToHost));
+    if (!st && (rh || ru || lambda)) {
+        // reuse the input state buffers as staging for the outputs
+        float* dlam = nullptr;
+        e = cudaMalloc(&dlam, ni * sizeof(float));
+        if (e == cudaSuccess) st = rcscm_get_state(c, 0, drh, dru, dlam, nullptr);
+        else st = map_cuda(e);
+        if (!st && rh) st = map_cuda(cudaMemcpy(rh, drh, ns * sizeof(float), cudaMemcpyDeviceToHost));
+        if (!st && ru) st = map_cuda(cudaMemcpy(ru, dru, ns * sizeof(float), cudaMemcpyDeviceToHost));
+        if (!st && lambda) st = map_cuda(cudaMemcpy(lambda, dlam, ni * sizeof(float), cudaMemcpyDeviceToHost));
+        if (dlam) cudaFree(dlam);
+    }
+    if (!st && c) {
+        const int s2 = rcscm_status(c, nullptr, nullptr);
+        if (s2 == RCSCM_ENULLSPACE || s2 == RCSCM_ENONFINITE) st = s2;
+    }
+    rcscm_destroy(c);
+    cudaFree(dx); cudaFree(da); cudaFree(dR); cudaFree(dh); cudaFree(drh); cudaFree(dru);
+    if (dl) cudaFree(dl);
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// Multichannel Wiener extraction of the target image, sm_103a.
+//
+// With the final parameters, the posterior mean of h_ij = a_i s_ij given x_ij
+// (Sec. II-B-1 model; the filter is named in Sec. II-A and Sec. IV-B) is
+//   h_ij = r_h a a^H (R^(x)_ij)^{-1} x_ij = w_ij a_i,
+//   w_ij = r_h rho^(ax)_ij / (r_u + r_h rho^(aa)_i),
+// where (R^(x))^{-1} a is expanded by Sherman-Morrison (Eq. (eq:rijxinv)) and
+// rho^(ax) = tau^(ax) + sigma^(ab) sigma^(bx) / lambda, rho^(aa) = tau^(aa) +
+// |sigma^(ab)|^2 / lambda (Sec. III-C-2).  One thread per slot; x is not read.
+#include "rcscm_internal.cuh"
+
+namespace rcscm {
+namespace {
+
+__global__ void __launch_bounds__(kSlotBlock) extract_kernel(DevState d, float2* __restrict__ h) {
+    __shared__ float2 sa[kMaxM];
+    const BlockMap bm = d.bmap[blockIdx.x];
+    const RowDesc* rd = d.rows + bm.row;
+    const int M = rd->M;
+    const int J = rd->J;
+    if (threadIdx.x < M) sa[threadIdx.x] = d.a32[(size_t)bm.row * kMaxM + threadIdx.x];
+    __syncthreads();
+    const int j = bm.j0 + threadIdx.x;
+    if (j >= J) return;
+    const RowConst c = d.rc[bm.row];
+    const float lam = d.lam[bm.row];
+    const int64_t s = rd->slot_off + j;
+    const float4 t = d.inv4[s];
+    const float rh = d.rh[s], ru = d.ru[s];
+    const float2 sab = make_float2(c.sab_re, c.sab_im);
+    const float2 rax = cadd(make_float2(t.x, t.y), cscale(cmul(sab, make_float2(t.z, t.w)), 1.0f / lam));
+    const float raa = c.taa + c.sab2 / lam;
+    const float wr = rh / (ru + rh * raa);
+    const float2 w = cscale(rax, wr);
+    float2* out = h + rd->out_off + (int64_t)j * M;
+    for (int m = 0; m < M; ++m) out[m] = cmul(w, sa[m]);
+}
+
+}  // namespace
+
+cudaError_t launch_extract(const DevState& d, int n_blocks, float2* h_out, cudaStream_t s) {
+    if (n_blocks <= 0) return cudaSuccess;
+    extract_kernel<<<n_blocks, kSlotBlock, 0, s>>>(d, h_out);
+    return cudaGetLastError();
+}
+
+}  // namespace rcscm

@@ -1,0 +1,149 @@
+// Internal types and device helpers shared by the CUDA translation units of
+// the rank-constrained SCM library (sm_103a).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rcscm.h"
+
+namespace rcscm {
+
+constexpr int kMaxM = RCSCM_MAX_M;
+constexpr int kSlotBlock = 256;   // threads per block of the slot-parallel kernels
+
+// Status bits (bit k-1 for status code k).
+constexpr int kFlagNullspace = 1 << (RCSCM_ENULLSPACE - 1);
+constexpr int kFlagNonfinite = 1 << (RCSCM_ENONFINITE - 1);
+constexpr int kFlagClamp = 1 << (RCSCM_ECLAMP - 1);
+
+// One row = one (utterance, frequency bin i).  Rows share nothing in any rule.
+struct RowDesc {
+    int64_t slot_off;       // first slot of the row in the per-slot arrays
+    int64_t out_off;        // first complex element of the row in the concatenated h_out
+    int64_t scratch_off;    // naive rule: first float of the row's R^u scratch
+    const float2* x;        // row start in the caller's x  (J x M complex64)
+    const double2* a;       // caller's a_i                 (M complex128)
+    const double2* Rp;      // caller's R'_i                (M x M complex128)
+    const double* lambda0;  // caller's lambda_i or nullptr
+    const float* rh0;       // caller's r^(h)_i.  (J floats)
+    const float* ru0;       // caller's r^(u)_i.  (J floats)
+    int J, M, prob, freq;
+};
+
+// Per-row FP32 constants used by the slot kernels (derived in FP64 by setup).
+struct __align__(16) RowConst {
+    float taa;      // tau^(aa)_i                   Eq. (eq:taa)
+    float taaM;     // tau^(aa)_i / M
+    float inv_taa;  // 1 / tau^(aa)_i
+    float sab2;     // |sigma^(ab)_i|^2
+    float sab_re;   // sigma^(ab)_i                  Eq. (eq:sap)
+    float sab_im;
+    float invM;     // 1 / M
+    float pad;
+};
+
+// A block of the slot-parallel kernels covers slots [j0, j0 + kSlotBlock) of one row.
+struct BlockMap {
+    int row;
+    int j0;
+};
+
+// Device arrays owned by a context.
+struct DevState {
+    RowDesc* rows;         // [R]
+    RowConst* rc;          // [R]
+    BlockMap* bmap;        // [n_blocks]
+    int* order;            // [R] rows by descending J (iterate launch order)
+    // FP64 setup outputs, fixed stride kMaxM per row
+    double2* b64;          // [R][8]
+    double* mu;            // [R][8]
+    double* lam0;          // [R]
+    double* taa64;         // [R]
+    double2* sab64;        // [R]
+    // FP32 copies for the slot kernels
+    float2* phi;           // [R][8][8]  rows: (R'^+ a)^H, Householder complement, b^H
+    float2* a32;           // [R][8]
+    float2* b32;           // [R][8]
+    float2* rp32;          // [R][8][8]  (naive rule)
+    // per-slot invariants and EM state
+    float4* inv4;          // [S] {tau_ax.re, tau_ax.im, sigma_bx.re, sigma_bx.im}
+    float* kap;            // [S] kappa = tau_xx - |tau_ax|^2 / tau_aa
+    float* rh;             // [S]
+    float* ru;             // [S]
+    float* lam;            // [R]
+    void* ru_hat;          // naive rules: packed Hermitian R^u per slot (float or double)
+    int* status;           // [1]
+};
+
+struct IterParams {
+    float c_a2;      // 1 / (alpha + 2)
+    float c_b;       // beta / (alpha + 2)
+    float ru_floor;
+    double c_a2_f64; // the same constants in FP64 (naive FP64 rule)
+    double c_b_f64;
+};
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {   // conj(a) * b
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+// acc += a * b
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+    return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+// acc += conj(a) * b
+__device__ __forceinline__ float2 cfmac(float2 a, float2 b, float2 acc) {
+    return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y)));
+}
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zmulc(double2 a, double2 b) {   // conj(a) * b
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 zscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double zabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// Hardware reciprocal approximation (MUFU.RCP, relative error ~1 ulp); inputs
+// here are positive normal numbers.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Butterfly sum over a warp: every lane ends with the same, order-fixed value.
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace rcscm
+
+// Launchers (defined in the .cu files, called by the C ABI in api.cu).
+namespace rcscm {
+cudaError_t launch_setup(const DevState& d, int n_rows, double null_tol, cudaStream_t s);
+cudaError_t launch_invariants(const DevState& d, int n_blocks, cudaStream_t s);
+cudaError_t launch_accel(const DevState& d, int n_rows, int max_j, int block, int n_iter,
+                         const IterParams& p, cudaStream_t s);
+// rows_by_m: device list of row indices grouped by M; count_by_m / first_by_m:
+// host arrays indexed by M (size kMaxM + 1) giving each group's size and start.
+cudaError_t launch_naive(const DevState& d, const int* rows_by_m, const int* count_by_m,
+                         const int* first_by_m, int n_iter, const IterParams& p, bool f64, cudaStream_t s);
+cudaError_t launch_extract(const DevState& d, int n_blocks, float2* h_out, cudaStream_t s);
+}  // namespace rcscm

@@ -1,0 +1,302 @@
+"""Python binding of librcscm.so (the C ABI declared in include/rcscm.h).
+
+Argument marshalling only: tensors are checked for device, dtype and layout and
+their addresses are handed to the library, which runs every step of the
+estimator in its CUDA kernels.  PyTorch provides device memory and streams.
+There is no fallback: if the library is missing or fails to load, every entry
+point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from ctypes import POINTER, c_double, c_float, c_int, c_int64, c_void_p
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librcscm.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "rcscm.h")
+
+OK, EINVAL, ENULLSPACE, ENONFINITE, ECLAMP, ECUDA, ENOMEM, ETIMEOUT = range(8)
+RULE_ACCEL, RULE_NAIVE, RULE_NAIVE_F64 = 0, 1, 2
+MAX_M = 8
+MAX_J_ACCEL = 4096
+FLT_MIN = float(np.finfo(np.float32).tiny)
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("I", c_int64), ("J", c_int64), ("M", c_int64),
+                ("x", c_void_p), ("a", c_void_p), ("Rp", c_void_p),
+                ("lambda0", c_void_p), ("rh0", c_void_p), ("ru0", c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("rule", c_int), ("alpha", c_double), ("beta", c_double),
+                ("ru_floor", c_float), ("null_tol", c_double), ("block", c_int),
+                ("iters_per_launch", c_int)]
+
+
+class RcscmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: rcscm error {code}: {strerror(code)}")
+
+
+_LIB = None
+
+
+def header_symbols() -> List[str]:
+    """Names of every function the public header declares."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rcscm_[a-z_0-9]+)\s*\(", src)))
+
+
+def lib():
+    """Load librcscm.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1908_01964_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64p = c_void_p, POINTER(c_int64)
+    sig = {
+        "rcscm_default_options": (None, [POINTER(Options)]),
+        "rcscm_strerror": (ctypes.c_char_p, [c_int]),
+        "rcscm_create": (c_int, [POINTER(vp), POINTER(Problem), c_int, POINTER(Options), vp]),
+        "rcscm_setup": (c_int, [vp, vp]),
+        "rcscm_iterate": (c_int, [vp, c_int, vp]),
+        "rcscm_extract": (c_int, [vp, vp, vp]),
+        "rcscm_get_state": (c_int, [vp, c_int, vp, vp, vp, vp]),
+        "rcscm_set_state": (c_int, [vp, c_int, vp, vp, vp, vp]),
+        "rcscm_get_setup": (c_int, [vp, c_int, vp, vp, vp, vp, vp, vp]),
+        "rcscm_get_invariants": (c_int, [vp, c_int, vp, vp, vp, vp]),
+        "rcscm_status": (c_int, [vp, POINTER(c_int), vp]),
+        "rcscm_info": (c_int, [vp, i64p, i64p, i64p]),
+        "rcscm_destroy": (None, [vp]),
+        "rcscm_solve_host": (c_int, [c_int64, c_int64, c_int64, vp, vp, vp, vp, vp, vp,
+                                     POINTER(Options), c_int, vp, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return lib().rcscm_strerror(code).decode()
+
+
+def _check(code: int, where: str, allow=(OK,)):
+    if code not in allow:
+        raise RcscmError(code, where)
+    return code
+
+
+def options(rule: str = "accel", alpha: float = 1.1, beta: float = 1e-16, ru_floor: float = FLT_MIN,
+            null_tol: float = 1e-6, block: int = 0, iters_per_launch: int = 0) -> Options:
+    o = Options()
+    lib().rcscm_default_options(ctypes.byref(o))
+    o.rule = {"accel": RULE_ACCEL, "naive": RULE_NAIVE, "naive64": RULE_NAIVE_F64}[rule]
+    o.alpha, o.beta, o.ru_floor, o.null_tol = alpha, beta, ru_floor, null_tol
+    o.block, o.iters_per_launch = block, iters_per_launch
+    return o
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return c_void_p(t.data_ptr())
+
+
+class Solver:
+    """A context over one or more utterances held in CUDA tensors.
+
+    Each problem is a dict with x (complex64 [I, J, M]), a (complex128 [I, M]),
+    Rp (complex128 [I, M, M]), rh0, ru0 (float32 [I, J]) and optionally lambda0
+    (float64 [I]).  The tensors must stay alive and unchanged while the Solver
+    exists (it keeps references to them).
+    """
+
+    def __init__(self, problems: Sequence[dict], rule: str = "accel", stream=None, **opts):
+        import torch
+        self._keep = []
+        arr = (Problem * len(problems))()
+        self.shapes = []
+        for k, p in enumerate(problems):
+            I, J, M = p["x"].shape
+            q = arr[k]
+            q.I, q.J, q.M = I, J, M
+            q.x = _dev(p["x"], torch.complex64, (I, J, M), "x")
+            q.a = _dev(p["a"], torch.complex128, (I, M), "a")
+            q.Rp = _dev(p["Rp"], torch.complex128, (I, M, M), "Rp")
+            q.rh0 = _dev(p["rh0"], torch.float32, (I, J), "rh0")
+            q.ru0 = _dev(p["ru0"], torch.float32, (I, J), "ru0")
+            lam0 = p.get("lambda0")
+            q.lambda0 = _dev(lam0, torch.float64, (I,), "lambda0") if lam0 is not None else None
+            self._keep.append(p)
+            self.shapes.append((I, J, M))
+        self.device = problems[0]["x"].device
+        self.opt = options(rule=rule, **opts)
+        self.rule = rule
+        ctx = c_void_p()
+        _check(lib().rcscm_create(ctypes.byref(ctx), arr, len(problems), ctypes.byref(self.opt), _stream(stream)),
+               "rcscm_create")
+        self.ctx = ctx
+
+    # -- lifecycle -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            lib().rcscm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- estimator steps -------------------------------------------------------
+    def setup(self, stream=None):
+        _check(lib().rcscm_setup(self.ctx, _stream(stream)), "rcscm_setup")
+
+    def iterate(self, n_iter: int, stream=None):
+        _check(lib().rcscm_iterate(self.ctx, int(n_iter), _stream(stream)), "rcscm_iterate")
+
+    @property
+    def out_elements(self) -> int:
+        return int(sum(I * J * M for I, J, M in self.shapes))
+
+    def extract(self, out=None, stream=None):
+        """Wiener-filtered target images, all utterances concatenated (complex64)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.out_elements, dtype=torch.complex64, device=self.device)
+        elif out.dtype != torch.complex64 or out.numel() != self.out_elements or not out.is_contiguous():
+            raise ValueError("out must be a contiguous complex64 tensor with one element per output")
+        _check(lib().rcscm_extract(self.ctx, c_void_p(out.data_ptr()), _stream(stream)), "rcscm_extract")
+        return out
+
+    def split(self, flat):
+        """Views of a concatenated extract() result, one [I, J, M] tensor per utterance."""
+        outs, o = [], 0
+        for I, J, M in self.shapes:
+            outs.append(flat[o:o + I * J * M].view(I, J, M))
+            o += I * J * M
+        return outs
+
+    def get_state(self, p: int = 0, stream=None):
+        import torch
+        I, J, _ = self.shapes[p]
+        rh = torch.empty((I, J), dtype=torch.float32, device=self.device)
+        ru = torch.empty_like(rh)
+        lam = torch.empty((I,), dtype=torch.float32, device=self.device)
+        _check(lib().rcscm_get_state(self.ctx, p, c_void_p(rh.data_ptr()), c_void_p(ru.data_ptr()),
+                                     c_void_p(lam.data_ptr()), _stream(stream)), "rcscm_get_state")
+        return rh, ru, lam
+
+    def set_state(self, p: int, rh=None, ru=None, lam=None, stream=None):
+        import torch
+        I, J, _ = self.shapes[p]
+        ptr = lambda t, shp, nm: _dev(t, torch.float32, shp, nm) if t is not None else None  # noqa: E731
+        _check(lib().rcscm_set_state(self.ctx, p, ptr(rh, (I, J), "rh"), ptr(ru, (I, J), "ru"),
+                                     ptr(lam, (I,), "lam"), _stream(stream)), "rcscm_set_state")
+
+    def get_setup(self, p: int = 0, stream=None) -> dict:
+        import torch
+        I, _, M = self.shapes[p]
+        kw = dict(device=self.device)
+        out = dict(b=torch.empty((I, M), dtype=torch.complex128, **kw),
+                   lambda0=torch.empty((I,), dtype=torch.float64, **kw),
+                   tau_aa=torch.empty((I,), dtype=torch.float64, **kw),
+                   sigma_ab=torch.empty((I,), dtype=torch.complex128, **kw),
+                   mu=torch.empty((I, M), dtype=torch.float64, **kw))
+        _check(lib().rcscm_get_setup(self.ctx, p, *(c_void_p(out[k].data_ptr()) for k in
+                                                    ("b", "lambda0", "tau_aa", "sigma_ab", "mu")),
+                                     _stream(stream)), "rcscm_get_setup")
+        return out
+
+    def get_invariants(self, p: int = 0, stream=None) -> dict:
+        import torch
+        I, J, _ = self.shapes[p]
+        kw = dict(device=self.device)
+        out = dict(tau_ax=torch.empty((I, J), dtype=torch.complex64, **kw),
+                   sigma_bx=torch.empty((I, J), dtype=torch.complex64, **kw),
+                   kappa=torch.empty((I, J), dtype=torch.float32, **kw))
+        _check(lib().rcscm_get_invariants(self.ctx, p, *(c_void_p(out[k].data_ptr()) for k in
+                                                         ("tau_ax", "sigma_bx", "kappa")),
+                                          _stream(stream)), "rcscm_get_invariants")
+        return out
+
+    def status(self, stream=None) -> int:
+        flags = c_int(0)
+        code = lib().rcscm_status(self.ctx, ctypes.byref(flags), _stream(stream))
+        if code == ECUDA:
+            raise RcscmError(code, "rcscm_status")
+        return code
+
+    def info(self) -> dict:
+        r, s, b = c_int64(), c_int64(), c_int64()
+        _check(lib().rcscm_info(self.ctx, ctypes.byref(r), ctypes.byref(s), ctypes.byref(b)), "rcscm_info")
+        return dict(rows=r.value, slots=s.value, device_bytes=b.value)
+
+
+def to_device(prob: dict, device="cuda") -> dict:
+    """Move a generator problem (numpy arrays) to CUDA tensors in the ABI's dtypes."""
+    import torch
+    out = dict(
+        x=torch.from_numpy(np.ascontiguousarray(prob["x"], np.complex64)).to(device),
+        a=torch.from_numpy(np.ascontiguousarray(prob["a"], np.complex128)).to(device),
+        Rp=torch.from_numpy(np.ascontiguousarray(prob["Rp"], np.complex128)).to(device),
+        rh0=torch.from_numpy(np.ascontiguousarray(prob["rh0"], np.float32)).to(device),
+        ru0=torch.from_numpy(np.ascontiguousarray(prob["ru0"], np.float32)).to(device),
+    )
+    if prob.get("lambda0") is not None:
+        out["lambda0"] = torch.from_numpy(np.ascontiguousarray(prob["lambda0"], np.float64)).to(device)
+    return out
+
+
+def solve_host(x, a, Rp, rh0, ru0, n_iter: int, lambda0=None, want_state: bool = True, **opts):
+    """One-shot solve from host (numpy) arrays through rcscm_solve_host."""
+    x = np.ascontiguousarray(x, np.complex64)
+    a = np.ascontiguousarray(a, np.complex128)
+    Rp = np.ascontiguousarray(Rp, np.complex128)
+    rh0 = np.ascontiguousarray(rh0, np.float32)
+    ru0 = np.ascontiguousarray(ru0, np.float32)
+    I, J, M = x.shape
+    h = np.empty_like(x)
+    rh = np.empty((I, J), np.float32) if want_state else None
+    ru = np.empty((I, J), np.float32) if want_state else None
+    lam = np.empty((I,), np.float32) if want_state else None
+    l0 = None if lambda0 is None else np.ascontiguousarray(lambda0, np.float64)
+    ptr = lambda v: None if v is None else c_void_p(v.ctypes.data)  # noqa: E731
+    o = options(**opts)
+    code = lib().rcscm_solve_host(I, J, M, ptr(x), ptr(a), ptr(Rp), ptr(l0), ptr(rh0), ptr(ru0),
+                                  ctypes.byref(o), int(n_iter), ptr(h), ptr(rh), ptr(ru), ptr(lam))
+    _check(code, "rcscm_solve_host", allow=(OK, ECLAMP))
+    return dict(h=h, rh=rh, ru=ru, lam=lam)

@@ -1,0 +1,345 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle on
+the same seeded inputs.  Needs a GPU; marked `gpu`."""
+import numpy as np
+import pytest
+
+from oracle import rcscm_oracle as O
+from paper_1908_01964_gb300 import synth
+from parity_util import (ALPHA, BETA, SDR_MIN_DB, TOL_FULL_RUN, TOL_ONE_ITER, compare, gpu_run,
+                         oracle_run, rel, report, sdr_db)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    from paper_1908_01964_gb300 import build, rcscm
+    build.build()
+    rcscm.lib()
+    torch.cuda.init()
+
+
+def _tiny(M, I=7, J=37, seed=3, K=4):
+    return synth.make_problem(synth.ProblemSpec(M=M, I=I, J=J, K=K, spacing=0.03), seed)
+
+
+# ------------------------------------------------------------------ A0 setup
+
+@pytest.mark.parametrize("M", [2, 3, 4, 5, 6, 7, 8])
+def test_setup_matches_oracle(M):
+    from paper_1908_01964_gb300 import rcscm as R
+    p = _tiny(M, I=9, seed=M)
+    st = O.setup(p["a"], p["Rp"])
+    with R.Solver([R.to_device(p)]) as s:
+        s.setup()
+        g = {k: v.cpu().numpy() for k, v in s.get_setup(0).items()}
+        assert s.status() == R.OK
+    muM = st.mu[:, -1:]
+    assert np.max(np.abs(g["mu"] - st.mu) / muM) < 1e-12
+    np.testing.assert_allclose(g["lambda0"], st.lam0, rtol=1e-9)
+    np.testing.assert_allclose(g["tau_aa"], st.tau_aa, rtol=1e-9)
+    # b is defined up to a phase: compare |b_gpu^H b_oracle| and phase-free products
+    overlap = np.abs(np.einsum("im,im->i", np.conj(g["b"]), st.b))
+    np.testing.assert_allclose(overlap, 1.0, atol=1e-10)
+    np.testing.assert_allclose(np.abs(g["sigma_ab"]), np.abs(st.sigma_ab), rtol=1e-9)
+    np.testing.assert_allclose(g["sigma_ab"], np.einsum("im,im->i", np.conj(p["a"]), g["b"]), atol=1e-12)
+
+
+def test_setup_uses_given_lambda0():
+    from paper_1908_01964_gb300 import rcscm as R
+    p = _tiny(4)
+    p["lambda0"] = np.linspace(0.3, 2.0, p["x"].shape[0])
+    with R.Solver([R.to_device(p)]) as s:
+        s.setup()
+        lam0 = s.get_setup(0)["lambda0"].cpu().numpy()
+        lam = s.get_state(0)[2].cpu().numpy()
+    np.testing.assert_array_equal(lam0, p["lambda0"])
+    np.testing.assert_allclose(lam, p["lambda0"], rtol=1e-7)
+
+
+# ------------------------------------------------------------------ A1 invariants
+
+@pytest.mark.parametrize("M", [2, 4, 6, 8])
+def test_invariants_match_oracle(M):
+    from paper_1908_01964_gb300 import rcscm as R
+    p = _tiny(M, I=11, J=300, seed=10 + M)
+    x = p["x"].astype(np.complex128)
+    st = O.setup(p["a"], p["Rp"])
+    inv = O.invariants(x, p["a"], st)
+    with R.Solver([R.to_device(p)]) as s:
+        s.setup()
+        g = {k: v.cpu().numpy() for k, v in s.get_invariants(0).items()}
+        b_gpu = s.get_setup(0)["b"].cpu().numpy()
+        sab_gpu = s.get_setup(0)["sigma_ab"].cpu().numpy()
+    assert rel(g["tau_ax"], inv.tau_ax) < 1e-5
+    kappa = inv.tau_xx - np.abs(inv.tau_ax) ** 2 / st.tau_aa[:, None]
+    assert np.all(g["kappa"] >= 0)
+    assert np.max(np.abs(g["kappa"] - kappa) / inv.tau_xx) < 1e-5
+    # sigma_bx follows the GPU's b; the product sigma_ab sigma_bx is phase free
+    assert rel(sab_gpu[:, None] * g["sigma_bx"], st.sigma_ab[:, None] * inv.sigma_bx) < 1e-5
+    assert rel(g["sigma_bx"], np.einsum("im,ijm->ij", np.conj(b_gpu), x)) < 1e-5
+
+
+# ------------------------------------------------------------------ A2-A4 accelerated iteration
+
+@pytest.mark.parametrize("name", ["plain-m2", "m4-small"])
+def test_accel_one_iteration(name):
+    if name == "plain-m2":
+        p = synth.make_workload(synth.workload("plain-m2"))[0]
+    else:
+        p = synth.make_problem(synth.ProblemSpec(M=4, I=129, J=333, K=20, spacing=0.03), 77)
+    (g,), st = gpu_run([p], 1)
+    o = oracle_run(p, 1)
+    e = compare(g, o)
+    report("accel_one_iter", case=name, gpu=e)
+    assert st == 0, st
+    assert max(e["rh"], e["ru"], e["lam"]) < TOL_ONE_ITER, e
+    assert e["sdr"] > SDR_MIN_DB, e
+
+
+def test_accel_full_run_plain_m2():
+    wl = synth.workload("plain-m2")
+    p = synth.make_workload(wl)[0]
+    (g,), st = gpu_run([p], wl.n_iter)
+    o = oracle_run(p, wl.n_iter)
+    e = compare(g, o)
+    report("accel_full_run_plain_m2", gpu=e)
+    assert st == 0
+    assert max(e["rh"], e["ru"], e["lam"]) < TOL_FULL_RUN, e
+    assert e["sdr"] > SDR_MIN_DB, e
+
+
+@pytest.mark.parametrize("M,J,block", [(2, 1, 0), (3, 2, 128), (4, 31, 0), (5, 129, 128), (6, 257, 256),
+                                       (7, 1000, 256), (8, 1023, 1024), (4, 2049, 512), (4, 4096, 0),
+                                       (2, 4096, 1024), (4, 700, 512)])
+def test_accel_edge_shapes(M, J, block):
+    p = synth.make_problem(synth.ProblemSpec(M=M, I=5, J=J, K=3, spacing=0.04), 1000 + J + M)
+    (g,), st = gpu_run([p], 3, block=block)
+    o = oracle_run(p, 3)
+    e = compare(g, o)
+    assert max(e["rh"], e["ru"], e["lam"]) < 1e-5, e
+    assert e["sdr"] > SDR_MIN_DB, e
+
+
+def test_batch_mixed_m_and_j():
+    specs = [synth.ProblemSpec(M=M, I=33, J=J, K=5, spacing=0.04)
+             for M, J in ((2, 200), (4, 1999), (6, 731), (4, 256), (3, 17), (8, 1500))]
+    probs = [synth.make_problem(s, 500 + k) for k, s in enumerate(specs)]
+    outs, st = gpu_run(probs, 10)
+    assert st == 0
+    for p, g in zip(probs, outs):
+        e = compare(g, oracle_run(p, 10))
+        assert max(e["rh"], e["ru"], e["lam"]) < 1e-4, e
+        assert e["sdr"] > SDR_MIN_DB, e
+
+
+def test_streaming_launches_equal_resident_bitwise():
+    p = _tiny(4, I=17, J=900, seed=4)
+    (g0,), _ = gpu_run([p], 7)
+    (g1,), _ = gpu_run([p], 7, iters_per_launch=1)
+    (g2,), _ = gpu_run([p], 7, iters_per_launch=3)
+    for k in ("rh", "ru", "lam", "h"):
+        np.testing.assert_array_equal(g0[k], g1[k])
+        np.testing.assert_array_equal(g0[k], g2[k])
+
+
+def test_resume_is_bitwise_and_deterministic():
+    p = _tiny(4, I=17, J=900, seed=5)
+    (a,), _ = gpu_run([p], 10)
+    (b,), _ = gpu_run([p], 10, chunks=[4, 6])
+    (c,), _ = gpu_run([p], 10)
+    for k in ("rh", "ru", "lam", "h"):
+        np.testing.assert_array_equal(a[k], b[k])
+        np.testing.assert_array_equal(a[k], c[k])
+
+
+def test_get_set_state_roundtrip():
+    import torch
+    from paper_1908_01964_gb300 import rcscm as R
+    p = _tiny(3, I=6, J=50)
+    with R.Solver([R.to_device(p)]) as s:
+        s.setup()
+        s.iterate(3)
+        rh, ru, lam = s.get_state(0)
+        s.iterate(2)
+        ref = [t.clone() for t in s.get_state(0)]
+        s.set_state(0, rh, ru, lam)
+        s.iterate(2)
+        got = s.get_state(0)
+        for u, v in zip(got, ref):
+            assert torch.equal(u, v)
+
+
+def test_rows_independent_in_batch():
+    # the same utterance alone and inside a batch gives bitwise-equal results
+    p = _tiny(4, I=9, J=400, seed=8)
+    q = _tiny(6, I=5, J=1200, seed=9)
+    (alone,), _ = gpu_run([p], 6, block=256)           # same block size -> same reduction tree
+    (first, _), _ = gpu_run([p, q], 6, block=256)
+    for k in ("rh", "ru", "lam", "h"):
+        np.testing.assert_array_equal(alone[k], first[k])
+
+
+# ------------------------------------------------------------------ A5 naive rule
+
+def _naive_fp32_error(p, n_iter):
+    """Error of the naive rule evaluated with the oracle's own formulas in single
+    precision (numpy complex64 / float32) against the FP64 oracle: the accuracy
+    FP32 arithmetic allows for the literal E-step, whose difference
+    r~_h - r~_h^2 a^H P a cancels when r~_h rho~ >> r~_u."""
+    st = O.setup(p["a"], p["Rp"])
+    rh, ru, lam = p["rh0"], p["ru0"], st.lam0.astype(np.float32)
+    for _ in range(n_iter):
+        rh, ru, lam = O.iterate_naive(rh, ru, lam, p["x"], p["a"], st, ALPHA, BETA, dtype=np.complex64)
+    o = oracle_run(p, n_iter, rule="naive")
+    return dict(rh=rel(rh, o["rh"]), ru=rel(ru, o["ru"]), lam=rel(lam, o["lam"])), o
+
+
+@pytest.mark.parametrize("M", [2, 3, 4, 5, 6, 8])
+def test_naive_fp32_one_iteration_within_fp32_accuracy(M):
+    p = synth.make_problem(synth.ProblemSpec(M=M, I=33, J=301, K=10, spacing=0.03), 40 + M)
+    e32, o = _naive_fp32_error(p, 1)
+    (g,), st = gpu_run([p], 1, rule="naive")
+    e = compare(g, o)
+    report("naive_one_iter", M=M, gpu=e, fp32_emulation=e32)
+    for k in ("rh", "ru", "lam"):
+        assert e[k] < max(TOL_ONE_ITER, 10 * e32[k]), (k, e, e32)
+    assert e["sdr"] > 40.0, e
+
+
+@pytest.mark.parametrize("M,n_iter", [(2, 50), (4, 20)])
+def test_naive_fp32_multi_iteration_stays_valid(M, n_iter):
+    """The FP32 naive rule over many passes: the projections onto r_h >= beta/(alpha+2)
+    and b^H R^u b >= 0 keep the model covariance positive definite; the error
+    against the FP64 oracle is what FP32 allows for this rule (reported)."""
+    p = synth.make_problem(synth.ProblemSpec(M=M, I=65, J=250, K=10, spacing=0.04), 60 + M)
+    (g,), st = gpu_run([p], n_iter, rule="naive")
+    o = oracle_run(p, n_iter, rule="naive")
+    e = compare(g, o)
+    report("naive_fp32_multi_iter", M=M, n_iter=n_iter, gpu=e, status=st)
+    assert st in (0, 4), st                      # OK or the clamp warning
+    for k in ("rh", "ru", "lam", "h"):
+        assert np.all(np.isfinite(g[k])), k
+    assert np.all(g["rh"] > 0) and np.all(g["ru"] > 0) and np.all(g["lam"] > 0)
+    assert e["sdr"] > 20.0, e
+
+
+@pytest.mark.parametrize("M", [2, 3, 4, 6, 8])
+def test_naive_f64_one_iteration(M):
+    p = synth.make_problem(synth.ProblemSpec(M=M, I=33, J=301, K=10, spacing=0.03), 40 + M)
+    (g,), st = gpu_run([p], 1, rule="naive64")
+    o = oracle_run(p, 1, rule="naive")
+    e = compare(g, o)
+    report("naive_f64_one_iter", M=M, gpu=e, status=st)
+    assert st == 0, st
+    assert max(e["rh"], e["ru"], e["lam"]) < TOL_ONE_ITER, e
+    assert e["sdr"] > SDR_MIN_DB, e
+
+
+def test_naive_f64_full_run_plain_m2():
+    wl = synth.workload("plain-m2")
+    p = synth.make_workload(wl)[0]
+    (g,), st = gpu_run([p], wl.n_iter, rule="naive64")
+    o = oracle_run(p, wl.n_iter, rule="naive")
+    e = compare(g, o)
+    report("naive_f64_full_run_plain_m2", gpu=e, status=st)
+    assert st == 0, st
+    assert max(e["rh"], e["ru"], e["lam"]) < TOL_FULL_RUN, e
+    assert e["sdr"] > SDR_MIN_DB, e
+
+
+def test_naive_f64_single_m4_full_size_sampled_rows():
+    wl = synth.workload("single-m4")
+    p = synth.make_workload(wl)[0]
+    (g,), st = gpu_run([p], wl.n_iter, rule="naive64")
+    I = p["x"].shape[0]
+    rows = [0, 1, 2, 300, 700, I - 1]
+    o = oracle_run(p, wl.n_iter, rule="naive", rows=rows)
+    e = compare(g, o, rows=rows)
+    report("naive_f64_single_m4_full_size", rows=len(rows), gpu=e, status=st)
+    assert st == 0, st
+    assert max(e["rh"], e["ru"], e["lam"]) < TOL_FULL_RUN, e
+    assert e["sdr"] > SDR_MIN_DB, e
+
+
+def test_naive_f64_gpu_agrees_with_accel_gpu_plain_m2():
+    """Two GPU rules that share no per-slot arithmetic agree over a full run."""
+    wl = synth.workload("plain-m2")
+    p = synth.make_workload(wl)[0]
+    (gn,), sn = gpu_run([p], wl.n_iter, rule="naive64")
+    (ga,), _ = gpu_run([p], wl.n_iter)
+    e = {k: rel(ga[k], gn[k]) for k in ("rh", "ru", "lam")}
+    e["sdr"] = sdr_db(ga["h"], gn["h"])
+    report("accel_vs_naive_f64_plain_m2", gpu=e, status=sn)
+    assert sn == 0
+    assert max(e["rh"], e["ru"], e["lam"]) < TOL_FULL_RUN, e
+    assert e["sdr"] > SDR_MIN_DB, e
+
+
+def test_naive_fp32_plain_m2_stays_valid():
+    """On the plain M=2 workload the FP32 naive rule hits its projections (status
+    ECLAMP) and drifts from the FP64 result; it must still return a valid model."""
+    wl = synth.workload("plain-m2")
+    p = synth.make_workload(wl)[0]
+    (gn,), sn = gpu_run([p], 5, rule="naive")
+    o = oracle_run(p, 5, rule="naive")
+    e = compare(gn, o)
+    report("naive_fp32_plain_m2_5iter", gpu=e, status=sn)
+    assert sn in (0, 4), sn
+    for k in ("rh", "ru", "lam", "h"):
+        assert np.all(np.isfinite(gn[k])), k
+    assert np.all(gn["rh"] > 0) and np.all(gn["ru"] > 0) and np.all(gn["lam"] > 0)
+
+
+# ------------------------------------------------------------------ status and host API
+
+def test_status_flags_full_rank_noise_scm():
+    from paper_1908_01964_gb300 import rcscm as R
+    p = _tiny(4)
+    p["Rp"] = p["Rp"] + 0.5 * np.eye(4)[None]          # not rank M-1 any more
+    with R.Solver([R.to_device(p)]) as s:
+        s.setup()
+        assert s.status() == R.ENULLSPACE
+        assert s.status() == R.OK                       # the word is cleared by the read
+
+
+def test_status_flags_nonfinite_input():
+    from paper_1908_01964_gb300 import rcscm as R
+    p = _tiny(4, J=64)
+    p["x"] = p["x"].copy()
+    p["x"][2, 5, 1] = np.nan
+    with R.Solver([R.to_device(p)]) as s:
+        s.setup()
+        s.iterate(2)
+        assert s.status() == R.ENONFINITE
+
+
+def test_solve_host_matches_device_path():
+    from paper_1908_01964_gb300 import rcscm as R
+    p = _tiny(4, I=13, J=250, seed=12)
+    r = R.solve_host(p["x"], p["a"], p["Rp"], p["rh0"], p["ru0"], 8)
+    (g,), _ = gpu_run([p], 8)
+    for k in ("rh", "ru", "lam", "h"):
+        np.testing.assert_array_equal(r[k], g[k])
+
+
+# ------------------------------------------------------------------ full-size workload (sampled rows)
+
+def test_single_m4_full_size_sampled_rows():
+    """The benchmarked workload (M=4, I=1025, J=1000, 100 passes, then the
+    Wiener filter) in the bench's launch configuration; the oracle runs on a
+    sample of rows (rows are independent), including the ill-conditioned
+    lowest bins and the Nyquist bin."""
+    wl = synth.workload("single-m4")
+    p = synth.make_workload(wl)[0]
+    (g,), st = gpu_run([p], wl.n_iter)
+    assert st == 0
+    I = p["x"].shape[0]
+    rows = sorted(set([0, 1, 2, 3, I - 1] + list(np.random.default_rng(0).choice(I, 11, replace=False))))
+    o = oracle_run(p, wl.n_iter, rows=rows)
+    e = compare(g, o, rows=rows)
+    report("accel_single_m4_full_size", rows=len(rows), gpu=e)
+    assert max(e["rh"], e["ru"], e["lam"]) < TOL_FULL_RUN, e
+    assert e["sdr"] > SDR_MIN_DB, e
+    assert np.all(np.isfinite(g["h"])) and np.all(g["ru"] > 0) and np.all(g["rh"] > 0)
