@@ -1,0 +1,62 @@
+"""The algebra the accelerated CUDA kernel evaluates, restated in FP64 numpy and
+checked against the oracle's printed second-stage forms (Sec. III-C-2).
+
+The kernel evaluates per slot (old r~_h, r~_u, lambda~):
+  rho~_ax = tau_ax + sigma_ab sigma_bx / lambda~,  gamma = r~_h / (r~_u + r~_h rho~_aa)
+  c = gamma rho~_ax,  Q = gamma r~_u
+  r_h = (Q + |c|^2 + beta) / (alpha + 2)
+  d = sigma_bx - c conj(sigma_ab),  B = Q |sigma_ab|^2 + |d|^2,  ell = B / r~_u
+  A = Q tau_aa + kappa + tau_aa |c - tau_ax / tau_aa|^2
+  lambda = mean_j ell,  r_u = (A + B / lambda) / M
+which must equal the printed forms exactly in exact arithmetic."""
+import numpy as np
+import pytest
+
+from oracle import rcscm_oracle as O
+from paper_1908_01964_gb300 import synth
+
+ALPHA, BETA = 1.1, 1e-16
+
+
+def kernel_form(rh, ru, lam, inv, st, M):
+    sab = st.sigma_ab[:, None]
+    sab2 = np.abs(st.sigma_ab)[:, None] ** 2
+    taa = st.tau_aa[:, None]
+    kappa = inv.tau_xx - np.abs(inv.tau_ax) ** 2 / taa
+    rtaa = taa + sab2 / lam[:, None]
+    rax = inv.tau_ax + sab * inv.sigma_bx / lam[:, None]
+    g = rh / (ru + rh * rtaa)
+    c = g * rax
+    Q = g * ru
+    rh_new = (Q + np.abs(c) ** 2 + BETA) / (ALPHA + 2)
+    d = inv.sigma_bx - c * np.conj(sab)
+    B = Q * sab2 + np.abs(d) ** 2
+    lam_new = np.mean(B / ru, axis=1)
+    A = Q * taa + kappa + taa * np.abs(c - inv.tau_ax / taa) ** 2
+    ru_new = (A + B / lam_new[:, None]) / M
+    return rh_new, ru_new, lam_new
+
+
+@pytest.mark.parametrize("M", [2, 3, 4, 8])
+def test_kernel_algebra_equals_printed_second_stage_rule(M):
+    p = synth.tiny(M=M, I=9, J=40, K=3, seed=100 + M)
+    x = p["x"].astype(complex)
+    st = O.setup(p["a"], p["Rp"])
+    inv = O.invariants(x, p["a"], st)
+    rh, ru, lam = p["rh0"].astype(float), p["ru0"].astype(float), st.lam0.copy()
+    for _ in range(8):
+        want = O.iterate_accel2(rh, ru, lam, inv, st, M, ALPHA, BETA)
+        got = kernel_form(rh, ru, lam, inv, st, M)
+        for u, v in zip(got, want):
+            assert np.linalg.norm(u - v) < 1e-12 * np.linalg.norm(v)
+            np.testing.assert_allclose(u, v, rtol=1e-8)   # elementwise: the printed r_u form cancels
+        rh, ru, lam = want
+
+
+def test_kernel_algebra_terms_are_non_negative():
+    p = synth.tiny(M=4, I=9, J=40, K=3, seed=7)
+    x = p["x"].astype(complex)
+    st = O.setup(p["a"], p["Rp"])
+    inv = O.invariants(x, p["a"], st)
+    kappa = inv.tau_xx - np.abs(inv.tau_ax) ** 2 / st.tau_aa[:, None]
+    assert np.all(kappa >= -1e-12 * inv.tau_xx)           # Cauchy-Schwarz in the R'^+ inner product
