@@ -49,6 +49,8 @@ extern "C" {
 #define RCSCM_ECUDA       5  /* a CUDA runtime call failed                         */
 #define RCSCM_ENOMEM      6  /* device allocation failed                           */
 #define RCSCM_ETIMEOUT    7  /* reserved: a bounded device wait gave up            */
+#define RCSCM_ECAPACITY   8  /* the problem does not fit the fixed scratch array of
+                                rcscm_solve_noalloc (nothing was launched)         */
 
 /* ---- update rules ------------------------------------------------------ */
 #define RCSCM_RULE_ACCEL  0  /* second-stage accelerated rule, Algorithm 2         */
@@ -165,6 +167,38 @@ int rcscm_solve_host(int64_t I, int64_t J, int64_t M, const void* x, const void*
                      const void* Rp, const double* lambda0, const float* rh0,
                      const float* ru0, const rcscm_options* opt, int n_iter,
                      void* h_out, float* rh, float* ru, float* lambda);
+
+/* Solve one utterance without allocating any device memory.  (The paper has no
+ * counterpart: this is a deployment variant of the accelerated solve.)
+ *
+ * For callers that cannot call cudaMalloc: a real-time audio thread, where an
+ * allocation may synchronise the device and stall for an unbounded time, or a
+ * host application that hands the library a fixed GPU memory budget and does
+ * not let it allocate more.  The caller passes device inputs (x, a, Rp,
+ * lambda0 (may be NULL), rh0, ru0, same layouts as rcscm_problem) and device
+ * outputs: rh, ru [I][J] float (may alias rh0, ru0), lambda [I] float, h_out
+ * complex64 [I][J][M], and status (a device int that receives the status bits
+ * of rcscm_status, or NULL).  The work is the same as rcscm_create +
+ * rcscm_setup + rcscm_iterate(n_iter) + rcscm_extract with opt->rule =
+ * RCSCM_RULE_ACCEL (other rules: EINVAL), enqueued on `stream`; the call does
+ * not synchronise and never calls cudaMalloc, cudaFree or any allocating
+ * routine.
+ *
+ * Working memory comes from one 32 MiB array in the library's device memory,
+ * reserved on every GPU that loads the library until the process exits.  A
+ * problem needs about 1.5 KB per frequency bin plus 20 B per slot (I*J): for
+ * example I = 1025, J = 1000 (about 22 MB) fits and I = 2049, J = 4000 does
+ * not.  A problem that does not fit returns RCSCM_ECAPACITY before anything is
+ * launched.  The first call on each device looks the array's address up (with
+ * that device current) and caches it; make that first call before any stream
+ * capture.  All calls on a device share the array: two calls whose GPU work
+ * overlaps (for example on two streams) race and corrupt each other's results,
+ * so serialise them.  Each call clears the parts of the array that must start
+ * at zero and overwrites the rest. */
+int rcscm_solve_noalloc(int64_t I, int64_t J, int64_t M, const void* x, const void* a, const void* Rp,
+                        const double* lambda0, const float* rh0, const float* ru0,
+                        const rcscm_options* opt, int n_iter, float* rh, float* ru, float* lambda,
+                        void* h_out, int* status, void* stream);
 
 #ifdef __cplusplus
 }

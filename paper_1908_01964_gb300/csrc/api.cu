@@ -104,6 +104,7 @@ const char* rcscm_strerror(int code) {
         case RCSCM_ECUDA: return "CUDA runtime error";
         case RCSCM_ENOMEM: return "device memory allocation failed";
         case RCSCM_ETIMEOUT: return "bounded device wait gave up";
+        case RCSCM_ECAPACITY: return "problem too large for the fixed scratch array of rcscm_solve_noalloc";
         default: return "unknown rcscm status code";
     }
 }

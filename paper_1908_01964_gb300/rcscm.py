@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librcscm.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "rcscm.h")
 
-OK, EINVAL, ENULLSPACE, ENONFINITE, ECLAMP, ECUDA, ENOMEM, ETIMEOUT = range(8)
+OK, EINVAL, ENULLSPACE, ENONFINITE, ECLAMP, ECUDA, ENOMEM, ETIMEOUT, ECAPACITY = range(9)
 RULE_ACCEL, RULE_NAIVE, RULE_NAIVE_F64 = 0, 1, 2
 MAX_M = 8
 MAX_J_ACCEL = 4096
@@ -80,6 +80,8 @@ def lib():
         "rcscm_destroy": (None, [vp]),
         "rcscm_solve_host": (c_int, [c_int64, c_int64, c_int64, vp, vp, vp, vp, vp, vp,
                                      POINTER(Options), c_int, vp, vp, vp, vp]),
+        "rcscm_solve_noalloc": (c_int, [c_int64, c_int64, c_int64, vp, vp, vp, vp, vp, vp,
+                                        POINTER(Options), c_int, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
