@@ -63,7 +63,7 @@ int valid_options(const rcscm_options* o) {
     if (o->rule != RCSCM_RULE_ACCEL && o->rule != RCSCM_RULE_NAIVE && o->rule != RCSCM_RULE_NAIVE_F64) return 0;
     if (!(o->alpha > -2.0) || !(o->beta >= 0.0)) return 0;
     if (!(o->null_tol > 0.0) || !(o->ru_floor >= 0.0f)) return 0;
-    if (o->block != 0 && o->block != 128 && o->block != 256 && o->block != 512 && o->block != 1024) return 0;
+    if (!accel_block_ok(o->block)) return 0;
     if (o->iters_per_launch < 0) return 0;
     return 1;
 }
@@ -114,8 +114,6 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
     if (!out) return RCSCM_EINVAL;
     *out = nullptr;
     if (!probs || n_probs < 1 || !opt || !valid_options(opt)) return RCSCM_EINVAL;
-    const int max_block = opt->block ? opt->block : 512;
-    const int max_spt = (max_block == 1024) ? 4 : 8;
     int64_t R = 0, S = 0, n_blocks = 0, naive_scratch = 0;
     int max_j = 0;
     for (int p = 0; p < n_probs; ++p) {
@@ -123,7 +121,7 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
         if (q.I < 1 || q.J < 1 || q.M < 2 || q.M > kMaxM) return RCSCM_EINVAL;
         if (!q.x || !q.a || !q.Rp || !q.rh0 || !q.ru0) return RCSCM_EINVAL;
         if (q.J > INT32_MAX / 2) return RCSCM_EINVAL;
-        if (opt->rule == RCSCM_RULE_ACCEL && q.J > (int64_t)max_block * max_spt) return RCSCM_EINVAL;
+        if (opt->rule == RCSCM_RULE_ACCEL && q.J > accel_max_j(opt->block)) return RCSCM_EINVAL;
         R += q.I;
         S += q.I * q.J;
         n_blocks += q.I * ((q.J + kSlotBlock - 1) / kSlotBlock);

@@ -15,6 +15,9 @@
 //       A = Q tau_aa + kappa + tau_aa |c - tau_ax / tau_aa|^2
 //     lambda <- (1/J) sum_j ell_j  (fixed-order block reduction)  Eq. (eq:1st_li)
 //     pass B: r_u <- (A + B / lambda) / M                         Eq. (eq:1st_ru)
+//   Each CTA dispatches on its row's exact chunk count NK = ceil(J / BLOCK), so
+//   only the last chunk carries a validity mask, and per-pass scalars use the
+//   hardware reciprocal with one Newton step instead of IEEE division.
 //   The pass-B form is Eq. (eq:1st_ru) with R^u written as
 //   gamma~ r~_u a a^H + (x - c a)(x - c a)^H and R_i^{-1} = R'^+ + b b^H / lambda
 //   (Eq. (eq:riinv)): a sum of non-negative terms, so FP32 keeps r_u > 0 without
@@ -30,39 +33,44 @@ namespace {
 
 // Sum over the block with one __syncthreads; `red` is double-buffered by the
 // pass parity so consecutive passes never race on it.  Every thread returns
-// the same, order-fixed value.
+// the same, order-fixed value.  A single-warp block needs no shared memory.
 template <int BLOCK>
-__device__ __forceinline__ float block_sum(float v, float (*red)[BLOCK / 32], int parity) {
+__device__ __forceinline__ float block_sum(float v, float (*red)[BLOCK / 32 > 0 ? BLOCK / 32 : 1], int parity) {
     constexpr int NW = BLOCK / 32;
     v = warp_sum(v);
-    const int lane = threadIdx.x & 31;
-    if (lane == 0) red[parity][threadIdx.x >> 5] = v;
-    __syncthreads();
-    float t = red[parity][lane & (NW - 1)];
+    if constexpr (NW == 1) {
+        return v;
+    } else {
+        const int lane = threadIdx.x & 31;
+        if (lane == 0) red[parity][threadIdx.x >> 5] = v;
+        __syncthreads();
+        float t = red[parity][lane & (NW - 1)];
 #pragma unroll
-    for (int o = NW / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    return t;
+        for (int o = NW / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        return t;
+    }
 }
 
-template <int BLOCK, int SPT>
-__global__ void __launch_bounds__(BLOCK) accel_kernel(DevState d, int n_iter, IterParams p) {
-    __shared__ float red[2][BLOCK / 32];
-    const int r = d.order[blockIdx.x];
-    const RowDesc* rd = d.rows + r;
-    const int J = rd->J;
-    const int64_t off = rd->slot_off;
-    const RowConst c = d.rc[r];
-    const int tid = threadIdx.x;
-    const int nk = (J + BLOCK - 1) / BLOCK;     // <= SPT, checked by the host
+// 1/x for positive normal x: hardware approximation refined by one Newton step.
+__device__ __forceinline__ float rcp_refined(float x) {
+    const float r = rcp_approx(x);
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
 
-    float4 t[SPT];
-    float kapM[SPT], rh[SPT], ru[SPT], B[SPT];
-    bool valid[SPT];
+// One row, NK chunks of BLOCK slots (slot j = k * BLOCK + threadIdx.x), kept in
+// registers for all n_iter passes.  Chunks 0..NK-2 are full; the last may be partial.
+template <int BLOCK, int NK>
+__device__ __forceinline__ void accel_row(const DevState& d, int r, int J, int64_t off, const RowConst& c,
+                                          int n_iter, const IterParams& p,
+                                          float (*red)[BLOCK / 32 > 0 ? BLOCK / 32 : 1]) {
+    const int tid = threadIdx.x;
+    const bool last_ok = (NK - 1) * BLOCK + tid < J;
+    float4 t[NK];
+    float kapM[NK], rh[NK], ru[NK], B[NK];
 #pragma unroll
-    for (int k = 0; k < SPT; ++k) {
+    for (int k = 0; k < NK; ++k) {
         const int j = k * BLOCK + tid;
-        valid[k] = (k < nk) && (j < J);
-        if (valid[k]) {
+        if (k < NK - 1 || last_ok) {
             t[k] = d.inv4[off + j];
             kapM[k] = d.kap[off + j] * c.invM;
             rh[k] = d.rh[off + j];
@@ -77,43 +85,40 @@ __global__ void __launch_bounds__(BLOCK) accel_kernel(DevState d, int n_iter, It
     }
 
     float lam = d.lam[r];
-    const float fJ = (float)J;
+    const float invJ = 1.0f / (float)J;
     for (int it = 0; it < n_iter; ++it) {
-        const float il = 1.0f / lam;
+        const float il = rcp_refined(lam);
         const float rtaa = fmaf(c.sab2, il, c.taa);          // rho~_aa, Eq. (eq:traa_accel)
         const float slr = c.sab_re * il, sli = c.sab_im * il;
         float part = 0.f;
 #pragma unroll
-        for (int k = 0; k < SPT; ++k) {
-            if (k < nk) {
-                const float pr = fmaf(slr, t[k].z, fmaf(-sli, t[k].w, t[k].x));
-                const float pi = fmaf(slr, t[k].w, fmaf(sli, t[k].z, t[k].y));
-                const float g = rh[k] * rcp_approx(fmaf(rh[k], rtaa, ru[k]));
-                const float cr = g * pr, ci = g * pi;
-                const float Q = g * ru[k];
-                const float rhat = fmaf(ci, ci, fmaf(cr, cr, Q));
-                const float dr = fmaf(-cr, c.sab_re, fmaf(-ci, c.sab_im, t[k].z));
-                const float di = fmaf(-ci, c.sab_re, fmaf(cr, c.sab_im, t[k].w));
-                const float Bk = fmaf(dr, dr, fmaf(di, di, Q * c.sab2));
-                if (valid[k]) part = fmaf(Bk, rcp_approx(ru[k]), part);
-                const float er = fmaf(-t[k].x, c.inv_taa, cr);
-                const float ei = fmaf(-t[k].y, c.inv_taa, ci);
-                ru[k] = fmaf(c.taaM, fmaf(er, er, fmaf(ei, ei, Q)), kapM[k]);    // A / M
-                B[k] = Bk;
-                rh[k] = fmaf(rhat, p.c_a2, p.c_b);
-            }
+        for (int k = 0; k < NK; ++k) {
+            const float pr = fmaf(slr, t[k].z, fmaf(-sli, t[k].w, t[k].x));
+            const float pi = fmaf(slr, t[k].w, fmaf(sli, t[k].z, t[k].y));
+            const float g = rh[k] * rcp_approx(fmaf(rh[k], rtaa, ru[k]));
+            const float cr = g * pr, ci = g * pi;
+            const float Q = g * ru[k];
+            const float rhat = fmaf(ci, ci, fmaf(cr, cr, Q));
+            const float dr = fmaf(-cr, c.sab_re, fmaf(-ci, c.sab_im, t[k].z));
+            const float di = fmaf(-ci, c.sab_re, fmaf(cr, c.sab_im, t[k].w));
+            const float Bk = fmaf(dr, dr, fmaf(di, di, Q * c.sab2));
+            if (k < NK - 1 || last_ok) part = fmaf(Bk, rcp_approx(ru[k]), part);
+            const float er = fmaf(-t[k].x, c.inv_taa, cr);
+            const float ei = fmaf(-t[k].y, c.inv_taa, ci);
+            ru[k] = fmaf(c.taaM, fmaf(er, er, fmaf(ei, ei, Q)), kapM[k]);    // A / M
+            B[k] = Bk;
+            rh[k] = fmaf(rhat, p.c_a2, p.c_b);
         }
-        lam = block_sum<BLOCK>(part, red, it & 1) / fJ;
-        const float ilM = c.invM / lam;
+        lam = block_sum<BLOCK>(part, red, it & 1) * invJ;
+        const float ilM = rcp_refined(lam) * c.invM;
 #pragma unroll
-        for (int k = 0; k < SPT; ++k)
-            if (k < nk) ru[k] = fmaxf(fmaf(B[k], ilM, ru[k]), p.ru_floor);
+        for (int k = 0; k < NK; ++k) ru[k] = fmaxf(fmaf(B[k], ilM, ru[k]), p.ru_floor);
     }
 
     bool clamp = false;
 #pragma unroll
-    for (int k = 0; k < SPT; ++k) {
-        if (valid[k]) {
+    for (int k = 0; k < NK; ++k) {
+        if (k < NK - 1 || last_ok) {
             const int j = k * BLOCK + tid;
             d.rh[off + j] = rh[k];
             d.ru[off + j] = ru[k];
@@ -128,33 +133,61 @@ __global__ void __launch_bounds__(BLOCK) accel_kernel(DevState d, int n_iter, It
 }
 
 template <int BLOCK, int SPT>
+__global__ void __launch_bounds__(BLOCK) accel_kernel(DevState d, int n_iter, IterParams p) {
+    __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
+    const int r = d.order[blockIdx.x];
+    const RowDesc* rd = d.rows + r;
+    const int J = rd->J;
+    const int64_t off = rd->slot_off;
+    const RowConst c = d.rc[r];
+    const int nk = (J + BLOCK - 1) / BLOCK;     // 1..SPT, checked by the host
+    // The row's exact chunk count selects the unrolled body (block-uniform branch).
+#define RCSCM_ROW(N) \
+    case N:          \
+        if constexpr (N <= SPT) accel_row<BLOCK, N>(d, r, J, off, c, n_iter, p, red); \
+        break;
+    switch (nk) {
+        RCSCM_ROW(1) RCSCM_ROW(2) RCSCM_ROW(3) RCSCM_ROW(4) RCSCM_ROW(5) RCSCM_ROW(6) RCSCM_ROW(7) RCSCM_ROW(8)
+        RCSCM_ROW(9) RCSCM_ROW(10) RCSCM_ROW(11) RCSCM_ROW(12) RCSCM_ROW(13) RCSCM_ROW(14) RCSCM_ROW(15)
+        RCSCM_ROW(16)
+        default: break;
+    }
+#undef RCSCM_ROW
+}
+
+template <int BLOCK, int SPT>
 cudaError_t launch_accel_t(const DevState& d, int n_rows, int n_iter, const IterParams& p, cudaStream_t s) {
     accel_kernel<BLOCK, SPT><<<n_rows, BLOCK, 0, s>>>(d, n_iter, p);
     return cudaGetLastError();
 }
 
+template <int BLOCK>
+cudaError_t launch_accel_b(const DevState& d, int n_rows, int spt, int n_iter, const IterParams& p, cudaStream_t s) {
+    if (spt <= 4) return launch_accel_t<BLOCK, 4>(d, n_rows, n_iter, p, s);
+    if constexpr (accel_max_spt(BLOCK) >= 8)
+        if (spt <= 8) return launch_accel_t<BLOCK, 8>(d, n_rows, n_iter, p, s);
+    if constexpr (accel_max_spt(BLOCK) >= 16)
+        if (spt <= 16) return launch_accel_t<BLOCK, 16>(d, n_rows, n_iter, p, s);
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
-// block: threads per row (0 = choose from max_j).  SPT is the smallest of {4, 8}
-// with block * SPT >= max_j.
+// The kernel keeps SPT = the smallest of {4, 8, 16} slots per thread that
+// covers the longest row, so its register budget matches the work list.
 cudaError_t launch_accel(const DevState& d, int n_rows, int max_j, int block, int n_iter,
                          const IterParams& p, cudaStream_t s) {
     if (n_rows <= 0) return cudaSuccess;
-    if (block == 0) {
-        if (max_j <= 512) block = 128;
-        else if (max_j <= 2048) block = 256;
-        else block = 512;
-    }
-    const int spt = (block * 4 >= max_j) ? 4 : 8;
-    if (block * spt < max_j) return cudaErrorInvalidValue;
-    switch (block * 10 + spt) {
-        case 1284: return launch_accel_t<128, 4>(d, n_rows, n_iter, p, s);
-        case 1288: return launch_accel_t<128, 8>(d, n_rows, n_iter, p, s);
-        case 2564: return launch_accel_t<256, 4>(d, n_rows, n_iter, p, s);
-        case 2568: return launch_accel_t<256, 8>(d, n_rows, n_iter, p, s);
-        case 5124: return launch_accel_t<512, 4>(d, n_rows, n_iter, p, s);
-        case 5128: return launch_accel_t<512, 8>(d, n_rows, n_iter, p, s);
-        case 10244: return launch_accel_t<1024, 4>(d, n_rows, n_iter, p, s);
+    if (block == 0) block = accel_default_block(max_j);
+    const int need = (max_j + block - 1) / block;
+    if (need > accel_max_spt(block)) return cudaErrorInvalidValue;
+    switch (block) {
+        case 32: return launch_accel_b<32>(d, n_rows, need, n_iter, p, s);
+        case 64: return launch_accel_b<64>(d, n_rows, need, n_iter, p, s);
+        case 128: return launch_accel_b<128>(d, n_rows, need, n_iter, p, s);
+        case 256: return launch_accel_b<256>(d, n_rows, need, n_iter, p, s);
+        case 512: return launch_accel_b<512>(d, n_rows, need, n_iter, p, s);
+        case 1024: return launch_accel_b<1024>(d, n_rows, need, n_iter, p, s);
         default: return cudaErrorInvalidValue;
     }
 }

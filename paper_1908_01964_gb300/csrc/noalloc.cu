@@ -100,11 +100,9 @@ extern "C" int rcscm_solve_noalloc(int64_t I, int64_t J, int64_t M, const void* 
         return RCSCM_EINVAL;
     if (opt->rule != RCSCM_RULE_ACCEL || opt->iters_per_launch < 0 || !(opt->alpha > -2.0) || !(opt->beta >= 0.0))
         return RCSCM_EINVAL;
-    if (opt->block != 0 && opt->block != 128 && opt->block != 256 && opt->block != 512 && opt->block != 1024)
-        return RCSCM_EINVAL;
+    if (!accel_block_ok(opt->block)) return RCSCM_EINVAL;
     if (I < 1 || J < 1 || M < 2 || M > kMaxM) return RCSCM_EINVAL;
-    const int max_block = opt->block ? opt->block : 512;
-    if (J > (int64_t)max_block * (max_block == 1024 ? 4 : 8)) return RCSCM_EINVAL;
+    if (J > accel_max_j(opt->block)) return RCSCM_EINVAL;
 
     // Layout of the fixed array for this call; reject what does not fit.
     if (I > (int64_t)kNoAllocScratchBytes || J > (int64_t)kNoAllocScratchBytes) return RCSCM_ECAPACITY;

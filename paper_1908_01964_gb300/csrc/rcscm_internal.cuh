@@ -135,6 +135,23 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 }  // namespace rcscm
 
+// Accelerated kernel shapes: threads per row (32 ... 1024) and the largest
+// number of slots each thread keeps in registers for that block size.
+__host__ __device__ constexpr int accel_max_spt(int block) {
+    return block >= 1024 ? 4 : (block <= 128 ? 16 : 8);
+}
+// Default block for rows of up to max_j slots: the smallest block that keeps
+// at most 8 slots per thread.
+inline int accel_default_block(int max_j) {
+    int b = 32;
+    while (b < 512 && b * 8 < max_j) b *= 2;
+    return b;
+}
+inline bool accel_block_ok(int block) {
+    return block == 0 || block == 32 || block == 64 || block == 128 || block == 256 || block == 512 || block == 1024;
+}
+inline int accel_max_j(int block) { return block ? block * accel_max_spt(block) : 512 * 8; }
+
 // Launchers (defined in the .cu files, called by the C ABI in api.cu).
 namespace rcscm {
 cudaError_t launch_setup(const DevState& d, int n_rows, double null_tol, cudaStream_t s);
