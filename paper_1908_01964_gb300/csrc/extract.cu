@@ -14,26 +14,39 @@ namespace {
 
 __global__ void __launch_bounds__(kSlotBlock) extract_kernel(DevState d, float2* __restrict__ h) {
     __shared__ float2 sa[kMaxM];
+    __shared__ __align__(16) float2 sh[kSlotBlock * kMaxM];
     const BlockMap bm = d.bmap[blockIdx.x];
     const RowDesc* rd = d.rows + bm.row;
     const int M = rd->M;
     const int J = rd->J;
+    const int n = min(kSlotBlock, J - bm.j0);            // slots of this block
     if (threadIdx.x < M) sa[threadIdx.x] = d.a32[(size_t)bm.row * kMaxM + threadIdx.x];
     __syncthreads();
-    const int j = bm.j0 + threadIdx.x;
-    if (j >= J) return;
-    const RowConst c = d.rc[bm.row];
-    const float lam = d.lam[bm.row];
-    const int64_t s = rd->slot_off + j;
-    const float4 t = d.inv4[s];
-    const float rh = d.rh[s], ru = d.ru[s];
-    const float2 sab = make_float2(c.sab_re, c.sab_im);
-    const float2 rax = cadd(make_float2(t.x, t.y), cscale(cmul(sab, make_float2(t.z, t.w)), 1.0f / lam));
-    const float raa = c.taa + c.sab2 / lam;
-    const float wr = rh / (ru + rh * raa);
-    const float2 w = cscale(rax, wr);
-    float2* out = h + rd->out_off + (int64_t)j * M;
-    for (int m = 0; m < M; ++m) out[m] = cmul(w, sa[m]);
+    const int t = threadIdx.x;
+    if (t < n) {
+        const RowConst c = d.rc[bm.row];
+        const float lam = d.lam[bm.row];
+        const int64_t s = rd->slot_off + bm.j0 + t;
+        const float4 tv = d.inv4[s];
+        const float rh = d.rh[s], ru = d.ru[s];
+        const float2 sab = make_float2(c.sab_re, c.sab_im);
+        const float2 rax = cadd(make_float2(tv.x, tv.y), cscale(cmul(sab, make_float2(tv.z, tv.w)), 1.0f / lam));
+        const float raa = c.taa + c.sab2 / lam;
+        const float2 w = cscale(rax, rh / (ru + rh * raa));
+        for (int m = 0; m < M; ++m) sh[t * M + m] = cmul(w, sa[m]);
+    }
+    __syncthreads();
+    // write the block's n * M outputs (contiguous) with coalesced 16-byte stores when aligned
+    float2* dst = h + rd->out_off + (int64_t)bm.j0 * M;
+    const int nc = n * M;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        const float4* s4 = reinterpret_cast<const float4*>(sh);
+        for (int e = t; e < nc / 2; e += blockDim.x) d4[e] = s4[e];
+        if ((nc & 1) && t == 0) dst[nc - 1] = sh[nc - 1];
+    } else {
+        for (int e = t; e < nc; e += blockDim.x) dst[e] = sh[e];
+    }
 }
 
 }  // namespace

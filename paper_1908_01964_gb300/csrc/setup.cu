@@ -1,8 +1,9 @@
 // Per-frequency setup (FP64) and per-slot invariants (FP32) of the
 // rank-constrained SCM estimator, sm_103a.
 //
-// setup_kernel   one group of 8 lanes per row (utterance, frequency i):
-//   R' <- (R' + R'^H)/2, cyclic complex Jacobi eigendecomposition,
+// setup_kernel   one group of 16 lanes per row (utterance, frequency i):
+//   R' <- (R' + R'^H)/2, Hermitian eigendecomposition (FP32 Jacobi sweeps, then
+//   FP64 iterative refinement of the eigenbasis),
 //   b_i = eigenvector of the smallest eigenvalue (Sec. II-B-1), lambda_i = the
 //   next eigenvalue unless given (Sec. II-B-3), (R')^+ from the remaining pairs
 //   (Eq. (eq:riinv)), tau^(aa)_i (Eq. (eq:taa)), sigma^(ab)_i (Eq. (eq:sap)),
@@ -24,195 +25,334 @@ namespace rcscm {
 namespace {
 
 constexpr int kSetupWarps = 4;
-constexpr int kGroupLanes = 8;                            // lanes per row (M <= 8)
-constexpr int kSetupRows = kSetupWarps * 32 / kGroupLanes; // rows per block
-constexpr int kJacobiMaxSweeps = 30;
+constexpr int kGroupLanes = 16;                             // lanes per row
+constexpr int kSetupRows = kSetupWarps * 32 / kGroupLanes;  // rows per block
+constexpr int kEntries = kMaxM * kMaxM / kGroupLanes;       // matrix entries per lane
+constexpr int kJacobiMaxSweeps32 = 12;
+constexpr int kRefineMaxSteps = 6;
 
-// One row per group of 8 lanes (4 rows per warp); lane k of a group owns index
-// k of its row.  Control flow that contains __syncwarp is uniform over the warp;
-// groups with less work (smaller M, converged, or past the last row) apply no
-// rotation in a step.
-__global__ void __launch_bounds__(kSetupWarps * 32)
-setup_kernel(DevState d, int n_rows, double null_tol) {
-    __shared__ double2 sA[kSetupRows][kMaxM][kMaxM];
-    __shared__ double2 sV[kSetupRows][kMaxM][kMaxM];
-    __shared__ double2 sa[kSetupRows][kMaxM];
-    __shared__ double2 sc[kSetupRows][kMaxM];
-    __shared__ int sperm[kSetupRows][kMaxM];
+// Complex arithmetic for the FP32 Jacobi sweep.
+template <class R> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+__device__ __forceinline__ float2 cx(float r, float i) { return make_float2(r, i); }
+template <class C> __device__ __forceinline__ C xadd(C a, C b) { return cx(a.x + b.x, a.y + b.y); }
+template <class C> __device__ __forceinline__ C xsub(C a, C b) { return cx(a.x - b.x, a.y - b.y); }
+template <class C, class R> __device__ __forceinline__ C xscale(C a, R s) { return cx(a.x * s, a.y * s); }
+template <class C> __device__ __forceinline__ C xmul(C a, C b) { return cx(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <class C> __device__ __forceinline__ C xmulc(C a, C b) { return cx(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
+template <class C> __device__ __forceinline__ auto xabs2(C a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float xrsqrt(float v) { return rsqrtf(v); }
 
-    const int g = threadIdx.x / kGroupLanes;
-    const int k = threadIdx.x % kGroupLanes;
-    const int r = blockIdx.x * kSetupRows + g;
-    const bool active = r < n_rows;
-    RowDesc rd;
-    if (active) rd = d.rows[r];
-    const int M = active ? rd.M : 0;
-    double2(*A)[kMaxM] = sA[g];
-    double2(*V)[kMaxM] = sV[g];
-
-    for (int e = k; e < M * M; e += kGroupLanes) {
-        const int m = e / M, n = e % M;
-        const double2 amn = rd.Rp[m * M + n];
-        const double2 anm = rd.Rp[n * M + m];
-        const double2 h = make_double2(0.5 * (amn.x + anm.x), 0.5 * (amn.y - anm.y));
-        A[m][n] = h;
-        V[m][n] = make_double2(m == n ? 1.0 : 0.0, 0.0);
-        d.rp32[(size_t)r * 64 + m * M + n] = make_float2((float)h.x, (float)h.y);
-    }
-    if (k < M) {
-        const double2 av = rd.a[k];
-        sa[g][k] = av;
-        d.a32[(size_t)r * kMaxM + k] = make_float2((float)av.x, (float)av.y);
-    }
-    __syncwarp();
-    const int Mw = __reduce_max_sync(0xffffffffu, M);
-
-    double fro2 = 0.0;
+// Cyclic Jacobi sweeps on the Hermitian matrix A of this lane's group (lane k
+// owns index k), accumulating the rotations into V: A <- U^H A U, V <- V U.
+// With A_pq = m e^{i phi} and h = A_qq - A_pp, the rotation
+//   U = [[c, s], [-s e^{-i phi}, c e^{-i phi}]],  cos(2 theta) = |h| / sqrt(h^2 + 4 m^2),
+//   c = cos(theta), s = sign(h) sin(theta)   (|theta| <= pi/4)
+// zeroes A_pq; c and s come from three reciprocal square roots.  Only columns
+// p, q of A are updated and mirrored into rows p, q (A stays Hermitian); the
+// 2 x 2 diagonal block is set in closed form.  Sweeps stop when the
+// off-diagonal mass is at most tol2 * |A|_F^2 in every group of the warp.
+// Control flow containing __syncwarp is warp-uniform.
+template <class R>
+__device__ void jacobi_sweeps(typename Cplx<R>::type (*A)[kMaxM], typename Cplx<R>::type (*V)[kMaxM], int M,
+                              int Mw, int k, R tol2, R skip2, int max_sweeps) {
+    using C = typename Cplx<R>::type;
+    R fro2 = R(0);
     for (int m = 0; m < M; ++m)
-        for (int n = 0; n < M; ++n) fro2 += zabs2(A[m][n]);
-
-    // ---- cyclic Jacobi: the rotation in the (p, q) plane zeroes A[p][q] ------
-    for (int sweep = 0; sweep < kJacobiMaxSweeps; ++sweep) {
-        double off = 0.0;
+        for (int n = 0; n < M; ++n) fro2 += xabs2(A[m][n]);
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        R off = R(0);
         for (int p = 0; p < M; ++p)
-            for (int q = p + 1; q < M; ++q) off += zabs2(A[p][q]);
-        const bool conv = !(off > 1e-32 * fro2);
+            for (int q = p + 1; q < M; ++q) off += xabs2(A[p][q]);
+        const bool conv = !(off > tol2 * fro2);
         if (__all_sync(0xffffffffu, conv)) break;
         for (int p = 0; p < Mw - 1; ++p) {
             for (int q = p + 1; q < Mw; ++q) {
-                double c = 1.0, s = 0.0;
-                double2 e = make_double2(1.0, 0.0);
+                R c = R(1), s = R(0), app = R(0), aqq = R(0), m = R(0);
+                C ce = cx(R(1), R(0)), se = cx(R(0), R(0));     // c conj(e), s conj(e)
                 bool rot = false;
                 if (!conv && q < M) {
-                    const double2 apq = A[p][q];
-                    const double m2 = zabs2(apq);
-                    const double app = A[p][p].x, aqq = A[q][q].x;
-                    if (m2 > 0.0 && m2 > 1e-36 * fabs(app * aqq)) {
-                        const double inv_mag = rsqrt(m2);
-                        const double zeta = 0.5 * (aqq - app) * inv_mag;
-                        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
-                        c = rsqrt(fma(t, t, 1.0));
-                        s = t * c;
-                        e = make_double2(apq.x * inv_mag, apq.y * inv_mag);   // exp(i phi)
+                    const C apq = A[p][q];
+                    const R m2 = xabs2(apq);
+                    app = A[p][p].x;
+                    aqq = A[q][q].x;
+                    if (m2 > R(0) && m2 > skip2 * fabs(app * aqq)) {
+                        const R h = aqq - app;
+                        const R inv_m = xrsqrt(m2);
+                        m = m2 * inv_m;
+                        const R r = xrsqrt(fma(h, h, R(4) * m2));
+                        const R u = fma(R(0.5) * fabs(h), r, R(0.5));
+                        const R ru = xrsqrt(u);
+                        c = u * ru;
+                        s = copysign(m * r * ru, h);
+                        const C ec = cx(apq.x * inv_m, -apq.y * inv_m);   // conj(e)
+                        ce = xscale(ec, c);
+                        se = xscale(ec, s);
                         rot = true;
                     }
                 }
                 __syncwarp();
-                // A <- A U, V <- V U with U = [[c, s], [-s e^{-i phi}, c e^{-i phi}]] on (p, q)
                 if (rot && k < M) {
-                    const double2 akp = A[k][p];
-                    const double2 eq = zmulc(e, A[k][q]);
-                    A[k][p] = zsub(zscale(akp, c), zscale(eq, s));
-                    A[k][q] = zadd(zscale(akp, s), zscale(eq, c));
-                    const double2 vkp = V[k][p];
-                    const double2 veq = zmulc(e, V[k][q]);
-                    V[k][p] = zsub(zscale(vkp, c), zscale(veq, s));
-                    V[k][q] = zadd(zscale(vkp, s), zscale(veq, c));
-                }
-                __syncwarp();
-                // A <- U^H A: rows p, q
-                if (rot && k < M) {
-                    const double2 apk = A[p][k];
-                    const double2 eaq = zmul(e, A[q][k]);
-                    A[p][k] = zsub(zscale(apk, c), zscale(eaq, s));
-                    A[q][k] = zadd(zscale(apk, s), zscale(eaq, c));
-                }
-                __syncwarp();
-                if (rot && k == 0) {
-                    A[p][q] = make_double2(0.0, 0.0);
-                    A[q][p] = make_double2(0.0, 0.0);
-                    A[p][p].y = 0.0;
-                    A[q][q].y = 0.0;
+                    if (k != p && k != q) {        // columns p, q of A U, mirrored into rows p, q
+                        const C akp = A[k][p], akq = A[k][q];
+                        const C np = xsub(xscale(akp, c), xmul(se, akq));
+                        const C nq = xadd(xscale(akp, s), xmul(ce, akq));
+                        A[k][p] = np;
+                        A[k][q] = nq;
+                        A[p][k] = cx(np.x, -np.y);
+                        A[q][k] = cx(nq.x, -nq.y);
+                    } else if (k == p) {           // the 2 x 2 diagonal block
+                        const R cs2m = R(2) * c * s * m;
+                        A[p][p] = cx(fma(c * c, app, fma(s * s, aqq, -cs2m)), R(0));
+                        A[q][q] = cx(fma(s * s, app, fma(c * c, aqq, cs2m)), R(0));
+                        A[p][q] = cx(R(0), R(0));
+                        A[q][p] = cx(R(0), R(0));
+                    }
+                    const C vkp = V[k][p], vkq = V[k][q];   // V <- V U
+                    V[k][p] = xsub(xscale(vkp, c), xmul(se, vkq));
+                    V[k][q] = xadd(xscale(vkp, s), xmul(ce, vkq));
                 }
                 __syncwarp();
             }
         }
     }
+}
 
-    // ---- ascending order of the eigenvalues --------------------------------
-    if (active && k == 0) {
-        int perm[kMaxM];
-        for (int i = 0; i < M; ++i) perm[i] = i;
-        for (int i = 0; i < M; ++i) {
-            int best = i;
-            for (int l = i + 1; l < M; ++l)
-                if (A[perm[l]][perm[l]].x < A[perm[best]][perm[best]].x) best = l;
-            const int tmp = perm[i];
-            perm[i] = perm[best];
-            perm[best] = tmp;
-        }
-        for (int i = 0; i < M; ++i) sperm[g][i] = perm[i];
+// Sum / maximum over the 16 lanes of a row group (xor offsets stay in the group).
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+    for (int o = kGroupLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double group_max(double v) {
+#pragma unroll
+    for (int o = kGroupLanes / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// One row per group of 16 lanes (2 rows per warp).  The eigendecomposition of
+// R' runs in two phases.  Phase 1: cyclic Jacobi sweeps in FP32 (lane k owns
+// index k) give approximate eigenvectors X.  Phase 2, FP64: iterative
+// refinement of the whole eigenbasis (Ogita and Aishima's method, written
+// here for Hermitian matrices):
+//   R = I - X^H X,  S = X^H R' X,  lambda_i = S_ii / (1 - R_ii),
+//   E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)   (i != j, separated),
+//   E_ij = R_ij / 2                                         (diagonal, clusters),
+//   X <- X (I + E),
+// which converges quadratically and consists of matrix products only, so the
+// lanes of a group share its M x M entries (at most 4 each).  Control flow that
+// contains warp-wide synchronisation is uniform over the warp.
+__global__ void __launch_bounds__(kSetupWarps * 32)
+setup_kernel(DevState d, int n_rows, double null_tol) {
+    __shared__ double2 sA[kSetupRows][kMaxM][kMaxM];    // R' (symmetrised)
+    __shared__ double2 sX[kSetupRows][kMaxM][kMaxM];    // eigenvectors (columns)
+    __shared__ double2 sR[kSetupRows][kMaxM][kMaxM];    // I - X^H X   (phase 1: FP32 A and V)
+    __shared__ double2 sS[kSetupRows][kMaxM][kMaxM];    // X^H R' X
+    __shared__ double2 sT[kSetupRows][kMaxM][kMaxM];    // R' X, then E
+    __shared__ double slam[kSetupRows][kMaxM];
+    __shared__ double2 sa[kSetupRows][kMaxM];
+    __shared__ double2 sc[kSetupRows][kMaxM];
+    __shared__ double srs[kSetupRows][kMaxM];
+    __shared__ int sperm[kSetupRows][kMaxM];
+
+    const int g = threadIdx.x / kGroupLanes;
+    const int l = threadIdx.x % kGroupLanes;
+    const int r = blockIdx.x * kSetupRows + g;
+    const bool active = r < n_rows;
+    RowDesc rd;
+    if (active) rd = d.rows[r];
+    const int M = active ? rd.M : 0;
+    const int MM = M * M;
+    double2(*A)[kMaxM] = sA[g];
+    double2(*X)[kMaxM] = sX[g];
+    double2(*Rm)[kMaxM] = sR[g];
+    double2(*S)[kMaxM] = sS[g];
+    double2(*T)[kMaxM] = sT[g];
+    float2(*A32)[kMaxM] = reinterpret_cast<float2(*)[kMaxM]>(&sR[g][0][0]);
+    float2(*V32)[kMaxM] = reinterpret_cast<float2(*)[kMaxM]>(&sR[g][kMaxM / 2][0]);
+
+    double afro2 = 0.0;
+    for (int e = l; e < MM; e += kGroupLanes) {
+        const int m = e / M, n = e % M;
+        const double2 amn = rd.Rp[m * M + n];
+        const double2 anm = rd.Rp[n * M + m];
+        const double2 h = make_double2(0.5 * (amn.x + anm.x), 0.5 * (amn.y - anm.y));
+        A[m][n] = h;
+        afro2 += zabs2(h);
+        const float2 hf = make_float2((float)h.x, (float)h.y);
+        A32[m][n] = hf;
+        V32[m][n] = make_float2(m == n ? 1.f : 0.f, 0.f);
+        d.rp32[(size_t)r * 64 + e] = hf;
+    }
+    if (l < M) {
+        const double2 av = rd.a[l];
+        sa[g][l] = av;
+        d.a32[(size_t)r * kMaxM + l] = make_float2((float)av.x, (float)av.y);
+    }
+    const double afro = sqrt(group_sum(afro2));
+    __syncwarp();
+    const int Mw = __reduce_max_sync(0xffffffffu, M);
+
+    // ---- phase 1: FP32 Jacobi sweeps ---------------------------------------------
+    jacobi_sweeps<float>(A32, V32, M, Mw, l, 1e-12f, 1e-14f, kJacobiMaxSweeps32);
+    for (int e = l; e < MM; e += kGroupLanes) {
+        const float2 v = V32[e / M][e % M];
+        X[e / M][e % M] = make_double2(v.x, v.y);
     }
     __syncwarp();
-    if (!active) return;          // no warp-level synchronisation follows
-    const int* perm = sperm[g];
-    const double mu1 = A[perm[0]][perm[0]].x;
-    const double mu2 = A[perm[1]][perm[1]].x;
-    const double muM = A[perm[M - 1]][perm[M - 1]].x;
-    if (k < M) d.mu[(size_t)r * kMaxM + k] = A[perm[k]][perm[k]].x;
 
+    // ---- phase 2: FP64 refinement of the eigenbasis -------------------------------
+    for (int step = 0; step < kRefineMaxSteps; ++step) {
+#pragma unroll
+        for (int t = 0; t < kEntries; ++t) {                     // R = I - X^H X, T = R' X
+            const int e = l + kGroupLanes * t;
+            if (e < MM) {
+                const int i = e / M, j = e % M;
+                double2 rr = make_double2(i == j ? 1.0 : 0.0, 0.0), tt = make_double2(0.0, 0.0);
+                for (int m = 0; m < M; ++m) {
+                    rr = zsub(rr, zmulc(X[m][i], X[m][j]));
+                    tt = zadd(tt, zmul(A[i][m], X[m][j]));
+                }
+                Rm[i][j] = rr;
+                T[i][j] = tt;
+            }
+        }
+        __syncwarp();
+        double so2 = 0.0, rr2 = 0.0;
+#pragma unroll
+        for (int t = 0; t < kEntries; ++t) {                     // S = X^H T
+            const int e = l + kGroupLanes * t;
+            if (e < MM) {
+                const int i = e / M, j = e % M;
+                double2 ss = make_double2(0.0, 0.0);
+                for (int m = 0; m < M; ++m) ss = zadd(ss, zmulc(X[m][i], T[m][j]));
+                S[i][j] = ss;
+                if (i != j) so2 += zabs2(ss);
+                rr2 += zabs2(Rm[i][j]);
+            }
+        }
+        const double delta = 2.0 * (sqrt(group_sum(so2)) + afro * sqrt(group_sum(rr2)));
+        __syncwarp();
+        if (l < M) slam[g][l] = S[l][l].x / (1.0 - Rm[l][l].x);
+        __syncwarp();
+        double emax = 0.0;
+#pragma unroll
+        for (int t = 0; t < kEntries; ++t) {                     // E (written over T)
+            const int e = l + kGroupLanes * t;
+            if (e < MM) {
+                const int i = e / M, j = e % M;
+                double2 ee;
+                if (i == j) {
+                    ee = make_double2(0.5 * Rm[i][j].x, 0.0);
+                } else {
+                    const double dl = slam[g][j] - slam[g][i];
+                    ee = fabs(dl) > delta ? zscale(zadd(S[i][j], zscale(Rm[i][j], slam[g][j])), 1.0 / dl)
+                                          : zscale(Rm[i][j], 0.5);
+                }
+                T[i][j] = ee;
+                emax = fmax(emax, zabs2(ee));
+            }
+        }
+        emax = group_max(emax);
+        __syncwarp();
+        double2 nx[kEntries];
+#pragma unroll
+        for (int t = 0; t < kEntries; ++t) {                     // X <- X + X E
+            const int e = l + kGroupLanes * t;
+            if (e < MM) {
+                const int i = e / M, j = e % M;
+                double2 v = X[i][j];
+                for (int k = 0; k < M; ++k) v = zadd(v, zmul(X[i][k], T[k][j]));
+                nx[t] = v;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < kEntries; ++t) {
+            const int e = l + kGroupLanes * t;
+            if (e < MM) X[e / M][e % M] = nx[t];
+        }
+        __syncwarp();
+        // |E| <= 1e-9: the next correction would be below FP64 rounding (quadratic convergence)
+        if (__all_sync(0xffffffffu, !(emax > 1e-18))) break;
+    }
+
+    // ---- ascending order of the eigenvalues (ranks) --------------------------------
+    if (l < M) {
+        const double li = slam[g][l];
+        int rank = 0;
+        for (int j = 0; j < M; ++j) {
+            const double lj = slam[g][j];
+            rank += (lj < li) || (lj == li && j < l);
+        }
+        sperm[g][rank] = l;
+    }
+    __syncwarp();
+    if (!active) return;                       // only group-local synchronisation follows
+    const unsigned gmask = 0xffffu << (threadIdx.x & 16);
+    const int* perm = sperm[g];
+    const double mu1 = slam[g][perm[0]];
+    const double mu2 = slam[g][perm[1]];
+    const double muM = slam[g][perm[M - 1]];
     const int k0 = perm[0];
-    if (k < M) {
-        const double2 bv = V[k][k0];
-        d.b64[(size_t)r * kMaxM + k] = bv;
-        d.b32[(size_t)r * kMaxM + k] = make_float2((float)bv.x, (float)bv.y);
+    if (l < M) {
+        d.mu[(size_t)r * kMaxM + l] = slam[g][perm[l]];
+        const double2 bv = X[l][k0];
+        d.b64[(size_t)r * kMaxM + l] = bv;
+        d.b32[(size_t)r * kMaxM + l] = make_float2((float)bv.x, (float)bv.y);
     }
-    // c_i = e_i^H a for the nonzero eigenpairs (sorted index i = 1..M-1)
-    if (k >= 1 && k < M) {
-        const int kk = perm[k];
+    // c_i = e_i^H a and 1/sqrt(mu_i) for the nonzero eigenpairs (sorted index i = 1..M-1)
+    if (l >= 1 && l < M) {
+        const int kk = perm[l];
         double2 acc = make_double2(0.0, 0.0);
-        for (int m = 0; m < M; ++m) acc = zadd(acc, zmulc(V[m][kk], sa[g][m]));
-        sc[g][k] = acc;
+        for (int m = 0; m < M; ++m) acc = zadd(acc, zmulc(X[m][kk], sa[g][m]));
+        sc[g][l] = acc;
+        srs[g][l] = rsqrt(slam[g][kk]);
     }
-    __syncwarp(0xffu << (threadIdx.x & 24));   // this group's lanes only
+    __syncwarp(gmask);
 
     double taa = 0.0;
-    for (int i = 1; i < M; ++i) taa += zabs2(sc[g][i]) / A[perm[i]][perm[i]].x;
+    for (int i = 1; i < M; ++i) taa += zabs2(sc[g][i]) * srs[g][i] * srs[g][i];
     double2 sab = make_double2(0.0, 0.0);
-    for (int m = 0; m < M; ++m) sab = zadd(sab, zmulc(sa[g][m], V[m][k0]));
+    for (int m = 0; m < M; ++m) sab = zadd(sab, zmulc(sa[g][m], X[m][k0]));
 
     const bool bad = !(mu2 > 0.0) || !(fabs(mu1) <= null_tol * muM) || !(taa > 0.0);
-    if (k == 0 && bad) atomicOr(d.status, kFlagNullspace);
+    if (l == 0 && bad) atomicOr(d.status, kFlagNullspace);
     const double lam0 = rd.lambda0 ? rd.lambda0[0] : mu2;
 
     // Householder vector for u = v / |v|, v_i = c_{i+1} / sqrt(mu_{i+1}), i = 0..M-2
     const double nv = sqrt(taa);
     const double inv_nv = nv > 0.0 ? 1.0 / nv : 0.0;
-    const double2 v0 = zscale(sc[g][1], rsqrt(A[perm[1]][perm[1]].x));
-    const double2 u0 = zscale(v0, inv_nv);
+    const double2 u0 = zscale(sc[g][1], srs[g][1] * inv_nv);
     const double au0 = sqrt(zabs2(u0));
     const double2 ph0 = au0 > 0.0 ? zscale(u0, 1.0 / au0) : make_double2(1.0, 0.0);
     // w = u - alpha e_0 with alpha = -ph0 |u| -> w_0 = ph0 (|u_0| + 1); |w|^2 = 2 + 2|u_0|
     const double two_over_wn2 = 2.0 / (2.0 + 2.0 * au0);
 
-    if (k < M) {
-        const int n = k;
-        float2* phi = d.phi + (size_t)r * 64;
-        // row 0: conj(g_n), g = R'^+ a = sum_i e_i c_i / mu_i
-        double2 gv = make_double2(0.0, 0.0);
-        double2 qn = make_double2(0.0, 0.0);    // q_n = sum_l conj(w_l) conj(e_{l+1}[n]) / sqrt(mu_{l+1})
-        for (int i = 1; i < M; ++i) {
-            const double mui = A[perm[i]][perm[i]].x;
-            const double rs = rsqrt(mui);
-            const double2 ein = V[n][perm[i]];
-            gv = zadd(gv, zscale(zmul(ein, sc[g][i]), rs * rs));
-            const double2 vl = zscale(sc[g][i], inv_nv * rs);                          // u_{i-1}
-            const double2 wl = (i == 1) ? zscale(ph0, au0 + 1.0) : vl;                 // w_{i-1}
-            qn = zadd(qn, zscale(zconj(zmul(wl, ein)), rs));
+    // Phi entries (kk, n): row 0 (R'^+ a)^H, rows 1..M-2 H L^H, row M-1 b^H
+    float2* phi = d.phi + (size_t)r * 64;
+    for (int e = l; e < MM; e += kGroupLanes) {
+        const int kk = e / M, n = e % M;
+        double2 val;
+        if (kk == 0) {                                   // conj(g_n), g = R'^+ a = sum_i e_i c_i / mu_i
+            double2 gv = make_double2(0.0, 0.0);
+            for (int i = 1; i < M; ++i)
+                gv = zadd(gv, zscale(zmul(X[n][perm[i]], sc[g][i]), srs[g][i] * srs[g][i]));
+            val = zconj(gv);
+        } else if (kk == M - 1) {
+            val = zconj(X[n][k0]);
+        } else {                                         // H L^H entry, L = [e_i / sqrt(mu_i)]
+            double2 qn = make_double2(0.0, 0.0);         // sum_l conj(w_l e_{l+1}[n]) / sqrt(mu_{l+1})
+            for (int i = 1; i < M; ++i) {
+                const double2 wl = (i == 1) ? zscale(ph0, au0 + 1.0) : zscale(sc[g][i], inv_nv * srs[g][i]);
+                qn = zadd(qn, zscale(zconj(zmul(wl, X[n][perm[i]])), srs[g][i]));
+            }
+            const double2 wk = zscale(sc[g][kk + 1], inv_nv * srs[g][kk + 1]);
+            val = zsub(zscale(zconj(X[n][perm[kk + 1]]), srs[g][kk + 1]), zscale(zmul(wk, qn), two_over_wn2));
         }
-        phi[0 * M + n] = make_float2((float)gv.x, (float)-gv.y);
-        for (int kk = 1; kk <= M - 2; ++kk) {
-            const double rs = rsqrt(A[perm[kk + 1]][perm[kk + 1]].x);
-            const double2 ekn = V[n][perm[kk + 1]];
-            const double2 wk = zscale(sc[g][kk + 1], inv_nv * rs);                    // w_kk = u_kk
-            double2 val = zscale(zconj(ekn), rs);
-            val = zsub(val, zscale(zmul(wk, qn), two_over_wn2));
-            phi[kk * M + n] = make_float2((float)val.x, (float)val.y);
-        }
-        const double2 bn = V[n][k0];
-        phi[(M - 1) * M + n] = make_float2((float)bn.x, (float)-bn.y);
+        phi[e] = make_float2((float)val.x, (float)val.y);
     }
-    if (k == 0) {
+    if (l == 0) {
         d.lam0[r] = lam0;
         d.taa64[r] = taa;
         d.sab64[r] = sab;
@@ -257,15 +397,29 @@ __device__ __forceinline__ void project_slot(const float2* __restrict__ phi, con
 
 __global__ void __launch_bounds__(kSlotBlock) invariants_kernel(DevState d) {
     __shared__ float2 sphi[kMaxM * kMaxM];
+    __shared__ __align__(16) float2 sx[kSlotBlock * kMaxM];
     const BlockMap bm = d.bmap[blockIdx.x];
     const RowDesc* rd = d.rows + bm.row;
     const int M = rd->M;
     const int J = rd->J;
+    const int n = min(kSlotBlock, J - bm.j0);            // slots of this block
     for (int e = threadIdx.x; e < M * M; e += blockDim.x) sphi[e] = d.phi[(size_t)bm.row * 64 + e];
+    // stage the block's x (n * M complex, contiguous) with coalesced 16-byte loads when aligned
+    const float2* src = rd->x + (size_t)bm.j0 * M;
+    const int nc = n * M;
+    if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        float4* d4 = reinterpret_cast<float4*>(sx);
+        for (int e = threadIdx.x; e < nc / 2; e += blockDim.x) d4[e] = s4[e];
+        if ((nc & 1) && threadIdx.x == 0) sx[nc - 1] = src[nc - 1];
+    } else {
+        for (int e = threadIdx.x; e < nc; e += blockDim.x) sx[e] = src[e];
+    }
     __syncthreads();
-    const int j = bm.j0 + threadIdx.x;
-    if (j >= J) return;
-    const float2* xs = rd->x + (size_t)j * M;
+    const int t = threadIdx.x;
+    if (t >= n) return;
+    const int j = bm.j0 + t;
+    const float2* xs = sx + t * M;
     float4 o;
     float kap;
     switch (M) {
