@@ -33,9 +33,10 @@ sys.path.insert(0, ROOT)
 METRIC = "EM TF-slot updates/s (I·J·iter/s) accel vs naive at M=4; % of HBM roofline"
 UNIT = "slot-updates/s"
 DATA = "synthetic: seeded plane-wave target + spherically isotropic diffuse noise (stands in for JNAS speech + measured RIRs)"
-# FP32-pipe operations of one slot update of the accelerated kernel (FFMA, FMUL,
-# FMNMX, each one lane-op), counted from csrc/iterate.cu; plus 2 MUFU reciprocals.
-ACCEL_FP32_OPS_PER_SLOT_ITER = 27
+# FP32 operations of one slot update of the accelerated kernel (each FFMA or FMUL
+# lane is one op; a packed f32x2 instruction is two), counted from
+# csrc/iterate.cu; plus 2 MUFU reciprocals per slot update.
+ACCEL_FP32_OPS_PER_SLOT_ITER = 26
 # Algorithmic bytes per slot of one accelerated launch: read tau_ax, sigma_bx
 # (16 B), kappa (4 B), r_h, r_u (8 B); write r_h, r_u (8 B).
 ACCEL_BYTES_PER_SLOT_LAUNCH = 36
@@ -314,7 +315,7 @@ def run_ours(args):
                     "frac": achieved / peak, "traffic": None,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz max SM clock",
                     "kernel": "accel_kernel (register-resident, all iterations in one launch)",
-                    "algorithmic": f"{ACCEL_FP32_OPS_PER_SLOT_ITER} FP32 ops + 2 MUFU per slot-iteration",
+                    "algorithmic": f"{ACCEL_FP32_OPS_PER_SLOT_ITER} FP32 ops + 2 MUFU per slot-iteration (f32x2 counts 2)",
                     "hbm_gbs_algorithmic": ACCEL_BYTES_PER_SLOT_LAUNCH * slots / (launch_ms / 1e3) / 1e9}
     elif args.rule == "accel":
         bytes_ = ACCEL_BYTES_PER_SLOT_LAUNCH * slots

@@ -15,9 +15,11 @@
 //       A = Q tau_aa + kappa + tau_aa |c - tau_ax / tau_aa|^2
 //     lambda <- (1/J) sum_j ell_j  (fixed-order block reduction)  Eq. (eq:1st_li)
 //     pass B: r_u <- (A + B / lambda) / M                         Eq. (eq:1st_ru)
-//   Each CTA dispatches on its row's exact chunk count NK = ceil(J / BLOCK), so
-//   only the last chunk carries a validity mask, and per-pass scalars use the
-//   hardware reciprocal with one Newton step instead of IEEE division.
+//   Each CTA dispatches on its row's exact count of chunk pairs, and the slot
+//   update runs on packed f32x2 instructions, one instruction for two slots.
+//   Per-pass scalars use the hardware reciprocal with one Newton step instead of
+//   IEEE division, and the r_u floor is part of kappa/M (all terms of r_u are
+//   non-negative), so r_u >= ru_floor needs no extra operation.
 //   The pass-B form is Eq. (eq:1st_ru) with R^u written as
 //   gamma~ r~_u a a^H + (x - c a)(x - c a)^H and R_i^{-1} = R'^+ + b b^H / lambda
 //   (Eq. (eq:riinv)): a sum of non-negative terms, so FP32 keeps r_u > 0 without
@@ -57,72 +59,126 @@ __device__ __forceinline__ float rcp_refined(float x) {
     return fmaf(r, fmaf(-x, r, 1.0f), r);
 }
 
-// One row, NK chunks of BLOCK slots (slot j = k * BLOCK + threadIdx.x), kept in
-// registers for all n_iter passes.  Chunks 0..NK-2 are full; the last may be partial.
-template <int BLOCK, int NK>
+// ---- packed pairs of FP32 values (sm_100+ f32x2 instructions) ---------------------
+// Two slots are updated by one packed instruction: each half is an ordinary
+// IEEE FP32 operation, so results equal the scalar code bit for bit.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float lo_of(f32x2 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float hi_of(f32x2 v) {
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return b;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 rcp2(f32x2 v) { return pk(rcp_approx(lo_of(v)), rcp_approx(hi_of(v))); }
+__device__ __forceinline__ f32x2 dup(float v) { return pk(v, v); }
+
+// One row with NP pairs of chunks (chunk k = slots k * BLOCK + threadIdx.x;
+// pair q = chunks 2q and 2q + 1), kept in registers for all n_iter passes.
+// Slots past the end of the row are padding that contributes exactly zero:
+// r_h = 0 and r_u = 1 throughout (their r_h offset beta/(alpha+2) is replaced by 0).
+template <int BLOCK, int NP>
 __device__ __forceinline__ void accel_row(const DevState& d, int r, int J, int64_t off, const RowConst& c,
                                           int n_iter, const IterParams& p,
                                           float (*red)[BLOCK / 32 > 0 ? BLOCK / 32 : 1]) {
     const int tid = threadIdx.x;
-    const bool last_ok = (NK - 1) * BLOCK + tid < J;
-    float4 t[NK];
-    float kapM[NK], rh[NK], ru[NK], B[NK];
+    f32x2 tr[NP], ti[NP], sr[NP], si[NP], kapM[NP], rh[NP], ru[NP], B[NP];
+    float cb_lo = p.c_b, cb_hi = p.c_b;                       // r_h offset of the last pair
 #pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        const int j = k * BLOCK + tid;
-        if (k < NK - 1 || last_ok) {
-            t[k] = d.inv4[off + j];
-            kapM[k] = d.kap[off + j] * c.invM;
-            rh[k] = d.rh[off + j];
-            ru[k] = d.ru[off + j];
-        } else {
-            t[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            kapM[k] = 0.f;
-            rh[k] = 0.f;
-            ru[k] = 1.f;
+    for (int q = 0; q < NP; ++q) {
+        float v[2][6];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = (2 * q + h) * BLOCK + tid;
+            if (j < J) {
+                const float4 t = d.inv4[off + j];
+                v[h][0] = t.x; v[h][1] = t.y; v[h][2] = t.z; v[h][3] = t.w;
+                v[h][4] = fmaf(d.kap[off + j], c.invM, p.ru_floor);   // r_u >= ru_floor by construction
+                v[h][5] = d.rh[off + j];
+            } else {
+                v[h][0] = v[h][1] = v[h][2] = v[h][3] = 0.f;
+                v[h][4] = 1.f;                                       // padding keeps r_u = 1
+                v[h][5] = 0.f;
+                if (q == NP - 1) { if (h == 0) cb_lo = 0.f; else cb_hi = 0.f; }
+            }
         }
-        B[k] = 0.f;
+        tr[q] = pk(v[0][0], v[1][0]);
+        ti[q] = pk(v[0][1], v[1][1]);
+        sr[q] = pk(v[0][2], v[1][2]);
+        si[q] = pk(v[0][3], v[1][3]);
+        kapM[q] = pk(v[0][4], v[1][4]);
+        rh[q] = pk(v[0][5], v[1][5]);
+        const int j0 = 2 * q * BLOCK + tid, j1 = j0 + BLOCK;
+        ru[q] = pk(j0 < J ? d.ru[off + j0] : 1.f, j1 < J ? d.ru[off + j1] : 1.f);
+        B[q] = 0;
     }
 
+    const f32x2 NSR = dup(-c.sab_re), NSI = dup(-c.sab_im), SI = dup(c.sab_im), SAB2 = dup(c.sab2);
+    const f32x2 NITAA = dup(-c.inv_taa), TAAM = dup(c.taaM), CA2 = dup(p.c_a2);
+    const f32x2 CB = dup(p.c_b), CB_LAST = pk(cb_lo, cb_hi);
     float lam = d.lam[r];
     const float invJ = 1.0f / (float)J;
     for (int it = 0; it < n_iter; ++it) {
         const float il = rcp_refined(lam);
-        const float rtaa = fmaf(c.sab2, il, c.taa);          // rho~_aa, Eq. (eq:traa_accel)
+        const f32x2 RTAA = dup(fmaf(c.sab2, il, c.taa));          // rho~_aa, Eq. (eq:traa_accel)
         const float slr = c.sab_re * il, sli = c.sab_im * il;
-        float part = 0.f;
+        const f32x2 SLR = dup(slr), SLI = dup(sli), NSLI = dup(-sli);
+        f32x2 part = dup(0.f);
 #pragma unroll
-        for (int k = 0; k < NK; ++k) {
-            const float pr = fmaf(slr, t[k].z, fmaf(-sli, t[k].w, t[k].x));
-            const float pi = fmaf(slr, t[k].w, fmaf(sli, t[k].z, t[k].y));
-            const float g = rh[k] * rcp_approx(fmaf(rh[k], rtaa, ru[k]));
-            const float cr = g * pr, ci = g * pi;
-            const float Q = g * ru[k];
-            const float rhat = fmaf(ci, ci, fmaf(cr, cr, Q));
-            const float dr = fmaf(-cr, c.sab_re, fmaf(-ci, c.sab_im, t[k].z));
-            const float di = fmaf(-ci, c.sab_re, fmaf(cr, c.sab_im, t[k].w));
-            const float Bk = fmaf(dr, dr, fmaf(di, di, Q * c.sab2));
-            if (k < NK - 1 || last_ok) part = fmaf(Bk, rcp_approx(ru[k]), part);
-            const float er = fmaf(-t[k].x, c.inv_taa, cr);
-            const float ei = fmaf(-t[k].y, c.inv_taa, ci);
-            ru[k] = fmaf(c.taaM, fmaf(er, er, fmaf(ei, ei, Q)), kapM[k]);    // A / M
-            B[k] = Bk;
-            rh[k] = fmaf(rhat, p.c_a2, p.c_b);
+        for (int q = 0; q < NP; ++q) {
+            const f32x2 pr = fma2(SLR, sr[q], fma2(NSLI, si[q], tr[q]));
+            const f32x2 pi = fma2(SLR, si[q], fma2(SLI, sr[q], ti[q]));
+            const f32x2 g = mul2(rh[q], rcp2(fma2(rh[q], RTAA, ru[q])));
+            const f32x2 cr = mul2(g, pr), ci = mul2(g, pi);
+            const f32x2 Q = mul2(g, ru[q]);
+            const f32x2 rhat = fma2(ci, ci, fma2(cr, cr, Q));
+            const f32x2 dr = fma2(cr, NSR, fma2(ci, NSI, sr[q]));
+            const f32x2 di = fma2(ci, NSR, fma2(cr, SI, si[q]));
+            const f32x2 Bk = fma2(dr, dr, fma2(di, di, mul2(Q, SAB2)));
+            part = fma2(Bk, rcp2(ru[q]), part);
+            const f32x2 er = fma2(tr[q], NITAA, cr);
+            const f32x2 ei = fma2(ti[q], NITAA, ci);
+            ru[q] = fma2(TAAM, fma2(er, er, fma2(ei, ei, Q)), kapM[q]);    // A / M
+            B[q] = Bk;
+            rh[q] = fma2(rhat, CA2, q == NP - 1 ? CB_LAST : CB);
         }
-        lam = block_sum<BLOCK>(part, red, it & 1) * invJ;
-        const float ilM = rcp_refined(lam) * c.invM;
+        lam = block_sum<BLOCK>(lo_of(part) + hi_of(part), red, it & 1) * invJ;
+        const f32x2 ILM = dup(rcp_refined(lam) * c.invM);
 #pragma unroll
-        for (int k = 0; k < NK; ++k) ru[k] = fmaxf(fmaf(B[k], ilM, ru[k]), p.ru_floor);
+        for (int q = 0; q < NP; ++q) ru[q] = fma2(B[q], ILM, ru[q]);
     }
 
     bool clamp = false;
 #pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        if (k < NK - 1 || last_ok) {
-            const int j = k * BLOCK + tid;
-            d.rh[off + j] = rh[k];
-            d.ru[off + j] = ru[k];
-            clamp |= (n_iter > 0) && (ru[k] <= p.ru_floor);
+    for (int q = 0; q < NP; ++q) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = (2 * q + h) * BLOCK + tid;
+            if (j < J) {
+                const float rhv = h ? hi_of(rh[q]) : lo_of(rh[q]);
+                const float ruv = h ? hi_of(ru[q]) : lo_of(ru[q]);
+                d.rh[off + j] = rhv;
+                d.ru[off + j] = ruv;
+                clamp |= (n_iter > 0) && (ruv <= p.ru_floor);
+            }
         }
     }
     if (clamp) atomicOr(d.status, kFlagClamp);
@@ -140,16 +196,14 @@ __global__ void __launch_bounds__(BLOCK) accel_kernel(DevState d, int n_iter, It
     const int J = rd->J;
     const int64_t off = rd->slot_off;
     const RowConst c = d.rc[r];
-    const int nk = (J + BLOCK - 1) / BLOCK;     // 1..SPT, checked by the host
-    // The row's exact chunk count selects the unrolled body (block-uniform branch).
+    const int np = (J + 2 * BLOCK - 1) / (2 * BLOCK);     // chunk pairs, 1..SPT/2 (checked by the host)
+    // The row's exact pair count selects the unrolled body (block-uniform branch).
 #define RCSCM_ROW(N) \
     case N:          \
-        if constexpr (N <= SPT) accel_row<BLOCK, N>(d, r, J, off, c, n_iter, p, red); \
+        if constexpr (2 * N <= SPT) accel_row<BLOCK, N>(d, r, J, off, c, n_iter, p, red); \
         break;
-    switch (nk) {
+    switch (np) {
         RCSCM_ROW(1) RCSCM_ROW(2) RCSCM_ROW(3) RCSCM_ROW(4) RCSCM_ROW(5) RCSCM_ROW(6) RCSCM_ROW(7) RCSCM_ROW(8)
-        RCSCM_ROW(9) RCSCM_ROW(10) RCSCM_ROW(11) RCSCM_ROW(12) RCSCM_ROW(13) RCSCM_ROW(14) RCSCM_ROW(15)
-        RCSCM_ROW(16)
         default: break;
     }
 #undef RCSCM_ROW
