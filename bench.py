@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--rule", choices=["accel", "naive"], default="accel")
     ap.add_argument("--iters-per-launch", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--persistent", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true", help="pick the launch shape with rcscm_autotune first")
+    ap.add_argument("--graph", action="store_true", help="replay the step as a CUDA graph")
     ap.add_argument("--naive-steps", type=int, default=None, help="timed naive steps (default min(steps, 10))")
     ap.add_argument("--no-naive", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -146,7 +149,8 @@ def dist_env():
 def make_inputs(name):
     from paper_1908_01964_gb300 import synth
     wl = synth.workload(name)
-    return wl, synth.make_workload(wl)
+    workers = min(16, os.cpu_count() or 1) if len(wl.specs) > 8 else 1
+    return wl, synth.make_workload(wl, workers=workers, inputs_only=True)
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -212,13 +216,23 @@ def cpu_baseline(p, wl, rule):
 
 # ----------------------------------------------------------------------------- our arm
 
-def time_steps(solver, h, n_iter, K, W, flush, stream, sampler=None, preroll_s=0.0):
+def time_steps(solver, h, n_iter, K, W, flush, stream, sampler=None, preroll_s=0.0, graph=False):
     import torch
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    if graph:
+        solver.graph_create(n_iter, h)
 
     def one(record):
         flush.zero_()
         e = [ev() for _ in range(4)] if record else None
+        if graph:                       # the whole step is one graph launch: no per-segment split
+            if record:
+                e[0].record(stream)
+            solver.graph_launch()
+            if record:
+                for k in (1, 2, 3):
+                    e[k].record(stream)
+            return e
         if record:
             e[0].record(stream)
         solver.setup()
@@ -273,12 +287,18 @@ def run_ours(args):
             dist.barrier()
 
     # ---------------- accelerated (or chosen) rule: the headline
-    solver = R.Solver(dprobs, rule=args.rule, iters_per_launch=args.iters_per_launch, block=args.block)
+    solver = R.Solver(dprobs, rule=args.rule, iters_per_launch=args.iters_per_launch, block=args.block,
+                      persistent=args.persistent)
     h = torch.empty(solver.out_elements, dtype=torch.complex64, device=dev)
+    tuned = None
+    if args.autotune and args.rule == "accel":
+        solver.setup()
+        tuned = solver.autotune(n_iter_probe=min(n_iter, 20))
     sampler = ClockSampler(torch.cuda.current_device() if ws == 1 else local) if rank == 0 or ws == 1 else None
     if sampler:
         sampler.wait_first()
-    one = time_steps(solver, h, n_iter, args.steps, args.warmup, flush, stream, sampler, args.clock_preroll)
+    one = time_steps(solver, h, n_iter, args.steps, args.warmup, flush, stream, sampler, args.clock_preroll,
+                     graph=args.graph)
     barrier()
     torch.cuda.synchronize()
     if sampler:
@@ -301,8 +321,19 @@ def run_ours(args):
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = ws * slots * n_iter / (ms_per_step / 1e3)
-    it_ms = statistics.mean(seg["iterate"])
+    it_ms = statistics.mean(seg["iterate"]) if not args.graph else None
     launches_per_iterate = 1 if args.iters_per_launch == 0 else -(-n_iter // args.iters_per_launch)
+    if it_ms is None:                   # graph: time the accelerated kernel alone once, outside the steps
+        tk = []
+        for _ in range(3):
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            solver.setup()
+            ea.record(stream)
+            solver.iterate(n_iter)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            tk.append(ea.elapsed_time(eb))
+        it_ms = min(tk)
     launch_ms = it_ms / launches_per_iterate
     iters_per_launch = n_iter if args.iters_per_launch == 0 else args.iters_per_launch
 
@@ -336,13 +367,18 @@ def run_ours(args):
         "config": {"workload": wl.name, "utterances": len(probs), "slots": slots, "n_iter": n_iter,
                    "M": sorted({s.M for s in wl.specs}), "I": sorted({s.I for s in wl.specs}),
                    "J": [min(s.J for s in wl.specs), max(s.J for s in wl.specs)], "rule": args.rule,
-                   "iters_per_launch": args.iters_per_launch, "block": args.block,
+                   "iters_per_launch": args.iters_per_launch,
+                   "block": tuned[0] if tuned else solver.opt.block,
+                   "persistent": tuned[1] if tuned else solver.opt.persistent, "autotuned": tuned is not None,
+                   "cuda_graph": args.graph,
                    "step": "setup + invariants + n_iter EM passes + Wiener extraction, inputs resident in HBM",
                    "l2": "flushed between timed steps (256 MB write outside the step's event brackets)",
                    "parallelism": f"replicas x{ws} (one utterance set per GPU, no collective)"},
-        "kernels_ms": {k: statistics.mean(v) for k, v in seg.items()},
+        "kernels_ms": ({k: statistics.mean(v) for k, v in seg.items()} if not args.graph
+                       else {"step_graph": ms_per_step, "iterate_alone": it_ms}),
         "roofline": roofline,
         "gpu_launches": args.steps * (2 + launches_per_iterate + 1),
+        "objective_after_step": float(solver.objective().sum()),
         "clocks": clocks,
     }
 

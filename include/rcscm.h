@@ -90,6 +90,9 @@ typedef struct {
     int    iters_per_launch; /* 0: every iteration of one rcscm_iterate call in one
                                 register-resident launch; k > 0: one launch per k
                                 iterations, state streamed through HBM between them    */
+    int    persistent;       /* 1: the accelerated kernel runs as a persistent grid of
+                                resident CTAs that take rows (longest first) from an
+                                atomic counter; 0 (default): one CTA per row            */
 } rcscm_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -159,6 +162,29 @@ void rcscm_destroy(rcscm_ctx* ctx);
 
 /* Static, NUL-terminated description of a status code. */
 const char* rcscm_strerror(int code);
+
+/* Observed-data log posterior of the model of Sec. II-B-1 with the current state,
+ * constants dropped: sum_ij [-log det R^(x) - x^H (R^(x))^{-1} x - (alpha+1) log r_h
+ * - beta/r_h], one value per utterance into the host array value[n_probs].  Each
+ * EM pass leaves it non-decreasing.  Synchronises `stream`. */
+int rcscm_objective(rcscm_ctx* ctx, double* value, void* stream);
+
+/* Autotuner of the accelerated kernel's launch shape: times n_iter_probe passes
+ * for every valid (block in {32,...,1024}) x (persistent 0/1) on this context's
+ * work list, restoring the EM state before each trial and at the end, and keeps
+ * the fastest in the context's options (also returned through the non-NULL
+ * pointers).  Results depend on the block size only through the order of the
+ * lambda reduction.  Allocates temporary device memory; synchronises `stream`.
+ * EINVAL for a naive-rule context. */
+int rcscm_autotune(rcscm_ctx* ctx, int n_iter_probe, int* chosen_block, int* chosen_persistent, void* stream);
+
+/* Capture one full solve step -- rcscm_setup, rcscm_iterate(n_iter),
+ * rcscm_extract(h_out) -- as a CUDA graph owned by the context (replacing any
+ * previous one); rcscm_graph_launch replays it on `stream`.  The graph keeps the
+ * context's and h_out's device addresses; the problem buffers must keep them
+ * too. */
+int rcscm_graph_create(rcscm_ctx* ctx, int n_iter, void* h_out);
+int rcscm_graph_launch(rcscm_ctx* ctx, void* stream);
 
 /* One-shot solve of a single utterance from HOST memory: copies x, a, Rp, rh0,
  * ru0 (same layouts as rcscm_problem, host pointers; lambda0 may be NULL) to the

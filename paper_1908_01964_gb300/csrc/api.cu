@@ -28,6 +28,11 @@ struct rcscm_ctx {
     int first_by_m[kMaxM + 1];
     std::vector<void*> allocs;
     int64_t bytes = 0;
+    int* first_block = nullptr;      // [n_probs + 1] first slot block of each utterance
+    double* obj_out = nullptr;       // [n_probs] objective per utterance (device)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
 };
 
 namespace {
@@ -55,6 +60,12 @@ int dalloc(rcscm_ctx* c, T** p, size_t n) {
 }
 
 void free_all(rcscm_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->cap_stream = nullptr;
     for (void* q : c->allocs) cudaFree(q);
     c->allocs.clear();
 }
@@ -65,6 +76,7 @@ int valid_options(const rcscm_options* o) {
     if (!(o->null_tol > 0.0) || !(o->ru_floor >= 0.0f)) return 0;
     if (!accel_block_ok(o->block)) return 0;
     if (o->iters_per_launch < 0) return 0;
+    if (o->persistent != 0 && o->persistent != 1) return 0;
     return 1;
 }
 
@@ -92,6 +104,7 @@ void rcscm_default_options(rcscm_options* opt) {
     opt->null_tol = 1e-6;
     opt->block = 0;
     opt->iters_per_launch = 0;
+    opt->persistent = 0;
 }
 
 const char* rcscm_strerror(int code) {
@@ -172,6 +185,15 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
             sc += q.J * q.M * q.M;
         }
     }
+    std::vector<int> first_block;
+    {
+        int64_t fb = 0;
+        for (int p = 0; p < n_probs; ++p) {
+            first_block.push_back((int)fb);
+            fb += probs[p].I * ((probs[p].J + kSlotBlock - 1) / kSlotBlock);
+        }
+        first_block.push_back((int)fb);
+    }
     std::vector<int> order((size_t)R);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return jrow[(size_t)x] > jrow[(size_t)y]; });
@@ -208,6 +230,16 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
     if (!st) st = dalloc(c, &d.lam, Rz);
     if (!st) st = dalloc(c, &d.status, 1);
     if (!st) st = dalloc(c, &c->naive_rows, Rz);
+    if (!st) st = dalloc(c, &d.counter, 1);
+    if (!st) st = dalloc(c, &d.obj_part, (size_t)n_blocks);
+    if (!st) st = dalloc(c, &c->first_block, (size_t)n_probs + 1);
+    if (!st) st = dalloc(c, &c->obj_out, (size_t)n_probs);
+    if (!st) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&d.n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            st = RCSCM_ECUDA;
+    }
     if (!st && opt->rule == RCSCM_RULE_NAIVE) {
         float* q = nullptr;
         st = dalloc(c, &q, (size_t)naive_scratch);
@@ -227,6 +259,9 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.bmap, bmap.data(), (size_t)n_blocks * sizeof(BlockMap), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.order, order.data(), Rz * sizeof(int), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->naive_rows, naive_rows.data(), Rz * sizeof(int), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->first_block, first_block.data(), first_block.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.status, 0, sizeof(int), cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);    // host tables go out of scope
     if (e != cudaSuccess) {
@@ -256,7 +291,7 @@ int rcscm_iterate(rcscm_ctx* c, int n_iter, void* stream) {
         const int k = std::min(chunk, n_iter - done);
         cudaError_t e;
         if (c->opt.rule == RCSCM_RULE_ACCEL)
-            e = launch_accel(c->d, (int)c->R, c->max_j, c->opt.block, k, p, cs);
+            e = launch_accel(c->d, (int)c->R, c->max_j, c->opt.block, k, p, c->opt.persistent != 0, cs);
         else
             e = launch_naive(c->d, c->naive_rows, c->count_by_m, c->first_by_m, k, p,
                              c->opt.rule == RCSCM_RULE_NAIVE_F64, cs);
@@ -358,6 +393,118 @@ void rcscm_destroy(rcscm_ctx* c) {
     cudaDeviceSynchronize();
     free_all(c);
     delete c;
+}
+
+int rcscm_objective(rcscm_ctx* c, double* value, void* stream) {
+    if (!c || !value) return RCSCM_EINVAL;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_objective(c->d, c->n_blocks, iter_params(c->opt), c->opt.alpha, c->opt.beta,
+                                     c->first_block, (int)c->probs.size(), c->obj_out, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(value, c->obj_out, c->probs.size() * sizeof(double), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    return map_cuda(e);
+}
+
+int rcscm_autotune(rcscm_ctx* c, int n_iter_probe, int* chosen_block, int* chosen_persistent, void* stream) {
+    if (!c || n_iter_probe < 1) return RCSCM_EINVAL;
+    if (c->opt.rule != RCSCM_RULE_ACCEL) return RCSCM_EINVAL;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    const size_t S = (size_t)c->S, R = (size_t)c->R;
+    float *rh = nullptr, *ru = nullptr, *lam = nullptr;
+    int* status = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&rh, S * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&ru, S * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&lam, R * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    auto copy_state = [&](bool save) {
+        cudaError_t x = cudaMemcpyAsync(save ? rh : c->d.rh, save ? c->d.rh : rh, S * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, cs);
+        if (x == cudaSuccess)
+            x = cudaMemcpyAsync(save ? ru : c->d.ru, save ? c->d.ru : ru, S * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+        if (x == cudaSuccess)
+            x = cudaMemcpyAsync(save ? lam : c->d.lam, save ? c->d.lam : lam, R * sizeof(float),
+                                cudaMemcpyDeviceToDevice, cs);
+        if (x == cudaSuccess)
+            x = cudaMemcpyAsync(save ? status : c->d.status, save ? c->d.status : status, sizeof(int),
+                                cudaMemcpyDeviceToDevice, cs);
+        return x;
+    };
+    if (e == cudaSuccess) e = copy_state(true);
+    const IterParams p = iter_params(c->opt);
+    float best = 3.0e38f;
+    int best_block = accel_default_block(c->max_j), best_pers = 0;
+    const int blocks[] = {32, 64, 128, 256, 512, 1024};
+    for (int bi = 0; bi < 6 && e == cudaSuccess; ++bi) {
+        const int b = blocks[bi];
+        if ((int64_t)b * accel_max_spt(b) < c->max_j) continue;
+        for (int pers = 0; pers <= 1 && e == cudaSuccess; ++pers) {
+            float t = 3.0e38f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                e = copy_state(false);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
+                if (e == cudaSuccess) e = launch_accel(c->d, (int)c->R, c->max_j, b, n_iter_probe, p, pers != 0, cs);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess && ms < t) t = ms;
+            }
+            if (e == cudaSuccess && t < best) {
+                best = t;
+                best_block = b;
+                best_pers = pers;
+            }
+        }
+    }
+    if (e == cudaSuccess) e = copy_state(false);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e == cudaSuccess) {
+        c->opt.block = best_block;
+        c->opt.persistent = best_pers;
+        if (chosen_block) *chosen_block = best_block;
+        if (chosen_persistent) *chosen_persistent = best_pers;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(rh);
+    cudaFree(ru);
+    cudaFree(lam);
+    cudaFree(status);
+    return map_cuda(e);
+}
+
+int rcscm_graph_create(rcscm_ctx* c, int n_iter, void* h_out) {
+    if (!c || n_iter < 0 || !h_out) return RCSCM_EINVAL;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return map_cuda(e);
+    e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return map_cuda(e);
+    int st = rcscm_setup(c, c->cap_stream);
+    if (!st) st = rcscm_iterate(c, n_iter, c->cap_stream);
+    if (!st) st = rcscm_extract(c, h_out, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e2 != cudaSuccess) return map_cuda(e2);
+    c->graph = g;
+    return map_cuda(cudaGraphInstantiate(&c->gexec, g, 0));
+}
+
+int rcscm_graph_launch(rcscm_ctx* c, void* stream) {
+    if (!c || !c->gexec) return RCSCM_EINVAL;
+    return map_cuda(cudaGraphLaunch(c->gexec, static_cast<cudaStream_t>(stream)));
 }
 
 int rcscm_solve_host(int64_t I, int64_t J, int64_t M, const void* x, const void* a, const void* Rp,

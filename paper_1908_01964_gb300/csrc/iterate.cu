@@ -28,6 +28,8 @@
 // The naive rule (per-slot M x M inverse) is in naive.cu.
 #include <float.h>
 
+#include <algorithm>
+
 #include "rcscm_internal.cuh"
 
 namespace rcscm {
@@ -189,9 +191,8 @@ __device__ __forceinline__ void accel_row(const DevState& d, int r, int J, int64
 }
 
 template <int BLOCK, int SPT>
-__global__ void __launch_bounds__(BLOCK) accel_kernel(DevState d, int n_iter, IterParams p) {
-    __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
-    const int r = d.order[blockIdx.x];
+__device__ __forceinline__ void accel_one_row(const DevState& d, int r, int n_iter, const IterParams& p,
+                                              float (*red)[BLOCK / 32 > 0 ? BLOCK / 32 : 1]) {
     const RowDesc* rd = d.rows + r;
     const int J = rd->J;
     const int64_t off = rd->slot_off;
@@ -209,19 +210,58 @@ __global__ void __launch_bounds__(BLOCK) accel_kernel(DevState d, int n_iter, It
 #undef RCSCM_ROW
 }
 
+// One CTA per row, rows in the order table (longest first).
 template <int BLOCK, int SPT>
-cudaError_t launch_accel_t(const DevState& d, int n_rows, int n_iter, const IterParams& p, cudaStream_t s) {
-    accel_kernel<BLOCK, SPT><<<n_rows, BLOCK, 0, s>>>(d, n_iter, p);
+__global__ void __launch_bounds__(BLOCK) accel_kernel(DevState d, int n_iter, IterParams p) {
+    __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
+    accel_one_row<BLOCK, SPT>(d, d.order[blockIdx.x], n_iter, p, red);
+}
+
+// Persistent variant: a fixed grid of resident CTAs takes rows from the order
+// table through an atomic counter (dynamic longest-first scheduling).
+template <int BLOCK, int SPT>
+__global__ void __launch_bounds__(BLOCK) accel_persistent_kernel(DevState d, int n_iter, IterParams p, int n_rows) {
+    __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
+    __shared__ int s_next;
+    for (;;) {
+        __syncthreads();                    // every thread is done with s_next and the previous row
+        if (threadIdx.x == 0) s_next = atomicAdd(d.counter, 1);
+        __syncthreads();
+        const int k = s_next;
+        if (k >= n_rows) break;
+        accel_one_row<BLOCK, SPT>(d, d.order[k], n_iter, p, red);
+    }
+}
+
+template <int BLOCK, int SPT>
+cudaError_t launch_accel_t(const DevState& d, int n_rows, int n_iter, const IterParams& p, bool persistent,
+                           cudaStream_t s) {
+    if (!persistent) {
+        accel_kernel<BLOCK, SPT><<<n_rows, BLOCK, 0, s>>>(d, n_iter, p);
+        return cudaGetLastError();
+    }
+    static const int per_sm = [] {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, accel_persistent_kernel<BLOCK, SPT>, BLOCK, 0) !=
+            cudaSuccess)
+            n = 1;
+        return n > 0 ? n : 1;
+    }();
+    const int grid = std::min(n_rows, per_sm * d.n_sm);
+    cudaError_t e = cudaMemsetAsync(d.counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    accel_persistent_kernel<BLOCK, SPT><<<grid, BLOCK, 0, s>>>(d, n_iter, p, n_rows);
     return cudaGetLastError();
 }
 
 template <int BLOCK>
-cudaError_t launch_accel_b(const DevState& d, int n_rows, int spt, int n_iter, const IterParams& p, cudaStream_t s) {
-    if (spt <= 4) return launch_accel_t<BLOCK, 4>(d, n_rows, n_iter, p, s);
+cudaError_t launch_accel_b(const DevState& d, int n_rows, int spt, int n_iter, const IterParams& p, bool persistent,
+                           cudaStream_t s) {
+    if (spt <= 4) return launch_accel_t<BLOCK, 4>(d, n_rows, n_iter, p, persistent, s);
     if constexpr (accel_max_spt(BLOCK) >= 8)
-        if (spt <= 8) return launch_accel_t<BLOCK, 8>(d, n_rows, n_iter, p, s);
+        if (spt <= 8) return launch_accel_t<BLOCK, 8>(d, n_rows, n_iter, p, persistent, s);
     if constexpr (accel_max_spt(BLOCK) >= 16)
-        if (spt <= 16) return launch_accel_t<BLOCK, 16>(d, n_rows, n_iter, p, s);
+        if (spt <= 16) return launch_accel_t<BLOCK, 16>(d, n_rows, n_iter, p, persistent, s);
     return cudaErrorInvalidValue;
 }
 
@@ -230,18 +270,18 @@ cudaError_t launch_accel_b(const DevState& d, int n_rows, int spt, int n_iter, c
 // The kernel keeps SPT = the smallest of {4, 8, 16} slots per thread that
 // covers the longest row, so its register budget matches the work list.
 cudaError_t launch_accel(const DevState& d, int n_rows, int max_j, int block, int n_iter,
-                         const IterParams& p, cudaStream_t s) {
+                         const IterParams& p, bool persistent, cudaStream_t s) {
     if (n_rows <= 0) return cudaSuccess;
     if (block == 0) block = accel_default_block(max_j);
     const int need = (max_j + block - 1) / block;
     if (need > accel_max_spt(block)) return cudaErrorInvalidValue;
     switch (block) {
-        case 32: return launch_accel_b<32>(d, n_rows, need, n_iter, p, s);
-        case 64: return launch_accel_b<64>(d, n_rows, need, n_iter, p, s);
-        case 128: return launch_accel_b<128>(d, n_rows, need, n_iter, p, s);
-        case 256: return launch_accel_b<256>(d, n_rows, need, n_iter, p, s);
-        case 512: return launch_accel_b<512>(d, n_rows, need, n_iter, p, s);
-        case 1024: return launch_accel_b<1024>(d, n_rows, need, n_iter, p, s);
+        case 32: return launch_accel_b<32>(d, n_rows, need, n_iter, p, persistent, s);
+        case 64: return launch_accel_b<64>(d, n_rows, need, n_iter, p, persistent, s);
+        case 128: return launch_accel_b<128>(d, n_rows, need, n_iter, p, persistent, s);
+        case 256: return launch_accel_b<256>(d, n_rows, need, n_iter, p, persistent, s);
+        case 512: return launch_accel_b<512>(d, n_rows, need, n_iter, p, persistent, s);
+        case 1024: return launch_accel_b<1024>(d, n_rows, need, n_iter, p, persistent, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -159,7 +159,7 @@ extern "C" int rcscm_solve_noalloc(int64_t I, int64_t J, int64_t M, const void* 
     const int chunk = opt->iters_per_launch > 0 ? opt->iters_per_launch : (n_iter > 0 ? n_iter : 1);
     for (int done = 0; e == cudaSuccess && done < n_iter; done += chunk) {
         const int k = n_iter - done < chunk ? n_iter - done : chunk;
-        e = launch_accel(d, (int)R, (int)J, opt->block, k, p, cs);
+        e = launch_accel(d, (int)R, (int)J, opt->block, k, p, false, cs);
     }
     if (e == cudaSuccess) e = launch_extract(d, (int)(R * nbpr), static_cast<float2*>(h_out), cs);
     if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, d.status, sizeof(int), cudaMemcpyDeviceToDevice, cs);

@@ -74,6 +74,9 @@ struct DevState {
     float* lam;            // [R]
     void* ru_hat;          // naive rules: packed Hermitian R^u per slot (float or double)
     int* status;           // [1]
+    int* counter;          // [1] row counter of the persistent accelerated kernel
+    double* obj_part;      // [n_blocks] objective partial sums (per slot block)
+    int n_sm;              // multiprocessors of the device
 };
 
 struct IterParams {
@@ -157,7 +160,11 @@ namespace rcscm {
 cudaError_t launch_setup(const DevState& d, int n_rows, double null_tol, cudaStream_t s);
 cudaError_t launch_invariants(const DevState& d, int n_blocks, cudaStream_t s);
 cudaError_t launch_accel(const DevState& d, int n_rows, int max_j, int block, int n_iter,
-                         const IterParams& p, cudaStream_t s);
+                         const IterParams& p, bool persistent, cudaStream_t s);
+// Observed-data log posterior: per slot block partials, then per-utterance sums
+// (block ranges [first_block[p], first_block[p + 1])) into out[p].
+cudaError_t launch_objective(const DevState& d, int n_blocks, const IterParams& p, double alpha, double beta,
+                             const int* first_block, int n_probs, double* out, cudaStream_t s);
 // rows_by_m: device list of row indices grouped by M; count_by_m / first_by_m:
 // host arrays indexed by M (size kMaxM + 1) giving each group's size and start.
 cudaError_t launch_naive(const DevState& d, const int* rows_by_m, const int* count_by_m,

@@ -36,7 +36,7 @@ class Problem(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("rule", c_int), ("alpha", c_double), ("beta", c_double),
                 ("ru_floor", c_float), ("null_tol", c_double), ("block", c_int),
-                ("iters_per_launch", c_int)]
+                ("iters_per_launch", c_int), ("persistent", c_int)]
 
 
 class RcscmError(RuntimeError):
@@ -82,6 +82,10 @@ def lib():
                                      POINTER(Options), c_int, vp, vp, vp, vp]),
         "rcscm_solve_noalloc": (c_int, [c_int64, c_int64, c_int64, vp, vp, vp, vp, vp, vp,
                                         POINTER(Options), c_int, vp, vp, vp, vp, vp, vp]),
+        "rcscm_objective": (c_int, [vp, POINTER(c_double), vp]),
+        "rcscm_autotune": (c_int, [vp, c_int, POINTER(c_int), POINTER(c_int), vp]),
+        "rcscm_graph_create": (c_int, [vp, c_int, vp]),
+        "rcscm_graph_launch": (c_int, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -102,12 +106,12 @@ def _check(code: int, where: str, allow=(OK,)):
 
 
 def options(rule: str = "accel", alpha: float = 1.1, beta: float = 1e-16, ru_floor: float = FLT_MIN,
-            null_tol: float = 1e-6, block: int = 0, iters_per_launch: int = 0) -> Options:
+            null_tol: float = 1e-6, block: int = 0, iters_per_launch: int = 0, persistent: int = 0) -> Options:
     o = Options()
     lib().rcscm_default_options(ctypes.byref(o))
     o.rule = {"accel": RULE_ACCEL, "naive": RULE_NAIVE, "naive64": RULE_NAIVE_F64}[rule]
     o.alpha, o.beta, o.ru_floor, o.null_tol = alpha, beta, ru_floor, null_tol
-    o.block, o.iters_per_launch = block, iters_per_launch
+    o.block, o.iters_per_launch, o.persistent = block, iters_per_launch, int(persistent)
     return o
 
 
@@ -254,6 +258,30 @@ class Solver:
                                                          ("tau_ax", "sigma_bx", "kappa")),
                                           _stream(stream)), "rcscm_get_invariants")
         return out
+
+    def objective(self, stream=None) -> np.ndarray:
+        """Observed-data log posterior per utterance (constants dropped), FP64."""
+        out = (c_double * len(self.shapes))()
+        _check(lib().rcscm_objective(self.ctx, out, _stream(stream)), "rcscm_objective")
+        return np.array(out[:], dtype=np.float64)
+
+    def autotune(self, n_iter_probe: int = 10, stream=None):
+        """Pick the fastest launch shape of the accelerated kernel for this work list."""
+        b, p = c_int(0), c_int(0)
+        _check(lib().rcscm_autotune(self.ctx, int(n_iter_probe), ctypes.byref(b), ctypes.byref(p), _stream(stream)),
+               "rcscm_autotune")
+        return b.value, p.value
+
+    def graph_create(self, n_iter: int, out):
+        """Capture setup + n_iter passes + extraction into `out` as a CUDA graph."""
+        import torch
+        if out.dtype != torch.complex64 or out.numel() != self.out_elements or not out.is_contiguous():
+            raise ValueError("out must be a contiguous complex64 tensor with one element per output")
+        self._graph_out = out
+        _check(lib().rcscm_graph_create(self.ctx, int(n_iter), c_void_p(out.data_ptr())), "rcscm_graph_create")
+
+    def graph_launch(self, stream=None):
+        _check(lib().rcscm_graph_launch(self.ctx, _stream(stream)), "rcscm_graph_launch")
 
     def status(self, stream=None) -> int:
         flags = c_int(0)

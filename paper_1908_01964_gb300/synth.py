@@ -203,8 +203,33 @@ def utterance_seed(wl: Workload, u: int) -> int:
     return int(np.random.SeedSequence([wl.seed, u]).generate_state(1, dtype=np.uint64)[0] >> 1)
 
 
-def make_workload(wl: Workload) -> List[dict]:
-    return [make_problem(s, utterance_seed(wl, u)) for u, s in enumerate(wl.specs)]
+_INPUT_KEYS = ("x", "a", "Rp", "rh0", "ru0", "spec", "seed")
+
+
+def _make_inputs_only(args):
+    spec, seed = args
+    p = make_problem(spec, seed)
+    return {k: p[k] for k in _INPUT_KEYS}
+
+
+def make_workload(wl: Workload, workers: int = 1, inputs_only: bool = False) -> List[dict]:
+    """Draw every utterance of a workload (optionally in `workers` spawned processes;
+    `inputs_only` drops the ground-truth arrays to save memory)."""
+    jobs = [(s, utterance_seed(wl, u)) for u, s in enumerate(wl.specs)]
+    if workers <= 1 or len(jobs) <= 1:
+        if inputs_only:
+            return [_make_inputs_only(j) for j in jobs]
+        return [make_problem(s, seed) for s, seed in jobs]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    fn = _make_inputs_only if inputs_only else _make_full
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(fn, jobs, chunksize=1))
+
+
+def _make_full(args):
+    spec, seed = args
+    return make_problem(spec, seed)
 
 
 def tiny(M: int = 3, I: int = 5, J: int = 7, K: int = 3, seed: int = 7, **kw) -> dict:
