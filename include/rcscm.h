@@ -228,6 +228,25 @@ int rcscm_solve_noalloc(int64_t I, int64_t J, int64_t M, const void* x, const vo
                         const rcscm_options* opt, int n_iter, float* rh, float* ru, float* lambda,
                         void* h_out, int* status, void* stream);
 
+/* Host-memory pipeline for utterances of one shape (I, J, M).  rcscm_host_create
+ * allocates device buffers for one utterance and splits its frequency rows into
+ * n_chunks contiguous ranges, each with its own context and stream (rows are
+ * independent in every rule).  rcscm_host_run copies x, a, Rp, rh0, ru0 from host
+ * memory (layouts of rcscm_problem), runs setup, n_iter passes of opt->rule and
+ * the Wiener filter, and copies h_out (complex64 [I][J][M]) and, when not NULL,
+ * rh, ru [I][J] and lambda [I] back; the copies of one chunk overlap the kernels
+ * of another.  Host buffers should be page-locked for the copies to overlap.
+ * lambda0 must be NULL (lambda_i starts at the smallest nonzero eigenvalue of
+ * R'_i).  rcscm_host_run synchronises before returning and reports the most
+ * severe status of the chunks.  Errors: EINVAL, ENOMEM, ECUDA, and the status
+ * codes of rcscm_status. */
+typedef struct rcscm_host rcscm_host;
+int rcscm_host_create(rcscm_host** plan, int64_t I, int64_t J, int64_t M, const rcscm_options* opt, int n_chunks);
+int rcscm_host_run(rcscm_host* plan, const void* x, const void* a, const void* Rp, const double* lambda0,
+                   const float* rh0, const float* ru0, int n_iter, void* h_out, float* rh, float* ru,
+                   float* lambda);
+void rcscm_host_destroy(rcscm_host* plan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -92,6 +92,8 @@ IterParams iter_params(const rcscm_options& o) {
 
 }  // namespace
 
+int* rcscm::ctx_status_word(rcscm_ctx* c) { return c ? c->d.status : nullptr; }
+
 extern "C" {
 
 void rcscm_default_options(rcscm_options* opt) {

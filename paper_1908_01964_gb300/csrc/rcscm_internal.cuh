@@ -157,6 +157,8 @@ inline int accel_max_j(int block) { return block ? block * accel_max_spt(block) 
 
 // Launchers (defined in the .cu files, called by the C ABI in api.cu).
 namespace rcscm {
+// Device status word of a context (api.cu), for the host pipeline's asynchronous status reads.
+int* ctx_status_word(rcscm_ctx* c);
 cudaError_t launch_setup(const DevState& d, int n_rows, double null_tol, cudaStream_t s);
 cudaError_t launch_invariants(const DevState& d, int n_blocks, cudaStream_t s);
 cudaError_t launch_accel(const DevState& d, int n_rows, int max_j, int block, int n_iter,

@@ -86,6 +86,9 @@ def lib():
         "rcscm_autotune": (c_int, [vp, c_int, POINTER(c_int), POINTER(c_int), vp]),
         "rcscm_graph_create": (c_int, [vp, c_int, vp]),
         "rcscm_graph_launch": (c_int, [vp, vp]),
+        "rcscm_host_create": (c_int, [POINTER(vp), c_int64, c_int64, c_int64, POINTER(Options), c_int]),
+        "rcscm_host_run": (c_int, [vp, vp, vp, vp, vp, vp, vp, c_int, vp, vp, vp, vp]),
+        "rcscm_host_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -309,6 +312,50 @@ def to_device(prob: dict, device="cuda") -> dict:
     if prob.get("lambda0") is not None:
         out["lambda0"] = torch.from_numpy(np.ascontiguousarray(prob["lambda0"], np.float64)).to(device)
     return out
+
+
+class HostPlan:
+    """rcscm_host_*: solves utterances of one shape from host (numpy) arrays with
+    chunked copy/compute overlap.  Use page-locked arrays for overlap."""
+
+    def __init__(self, I: int, J: int, M: int, n_chunks: int = 4, rule: str = "accel", **opts):
+        self.shape = (I, J, M)
+        self.opt = options(rule=rule, **opts)
+        plan = c_void_p()
+        _check(lib().rcscm_host_create(ctypes.byref(plan), I, J, M, ctypes.byref(self.opt), int(n_chunks)),
+               "rcscm_host_create")
+        self.plan = plan
+
+    def run_ptrs(self, x, a, Rp, rh0, ru0, n_iter, h_out, rh=None, ru=None, lam=None) -> int:
+        """Run on raw host addresses (ints); returns the status code."""
+        v = lambda p: None if p is None else c_void_p(p)  # noqa: E731
+        return lib().rcscm_host_run(self.plan, v(x), v(a), v(Rp), None, v(rh0), v(ru0), int(n_iter), v(h_out),
+                                    v(rh), v(ru), v(lam))
+
+    def run(self, prob: dict, n_iter: int, want_state: bool = True) -> dict:
+        I, J, M = self.shape
+        arrs = dict(x=np.ascontiguousarray(prob["x"], np.complex64), a=np.ascontiguousarray(prob["a"], np.complex128),
+                    Rp=np.ascontiguousarray(prob["Rp"], np.complex128),
+                    rh0=np.ascontiguousarray(prob["rh0"], np.float32), ru0=np.ascontiguousarray(prob["ru0"], np.float32))
+        out = dict(h=np.empty((I, J, M), np.complex64))
+        if want_state:
+            out.update(rh=np.empty((I, J), np.float32), ru=np.empty((I, J), np.float32), lam=np.empty((I,), np.float32))
+        ad = lambda k, d: d[k].ctypes.data if k in d else None  # noqa: E731
+        code = self.run_ptrs(ad("x", arrs), ad("a", arrs), ad("Rp", arrs), ad("rh0", arrs), ad("ru0", arrs), n_iter,
+                             out["h"].ctypes.data, ad("rh", out), ad("ru", out), ad("lam", out))
+        _check(code, "rcscm_host_run", allow=(OK, ECLAMP))
+        return out
+
+    def close(self):
+        if getattr(self, "plan", None) is not None and self.plan.value:
+            lib().rcscm_host_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve_host(x, a, Rp, rh0, ru0, n_iter: int, lambda0=None, want_state: bool = True, **opts):

@@ -324,6 +324,22 @@ def test_solve_host_matches_device_path():
         np.testing.assert_array_equal(r[k], g[k])
 
 
+@pytest.mark.parametrize("n_chunks", [1, 3])
+def test_host_plan_equals_device_path(n_chunks):
+    """rcscm_host_run (chunked host pipeline) returns bit for bit what the
+    device-resident context returns: rows are independent and every chunk uses
+    the same kernel shape."""
+    from paper_1908_01964_gb300 import rcscm as R
+    p = _tiny(4, I=29, J=700, seed=14)
+    plan = R.HostPlan(*p["x"].shape, n_chunks=n_chunks)
+    for _ in range(2):                          # the plan is reusable
+        r = plan.run(p, 9)
+        (g,), _ = gpu_run([p], 9)
+        for k in ("rh", "ru", "lam", "h"):
+            np.testing.assert_array_equal(r[k], g[k])
+    plan.close()
+
+
 # ------------------------------------------------------------------ full-size workload (sampled rows)
 
 def test_single_m4_full_size_sampled_rows():
