@@ -19,8 +19,10 @@ first demixing row.
 
 Readings where the paper is silent (each also listed in the design notes):
   * Setup: R' is symmetrised, and exactly one eigenvalue (the smallest) is taken
-    as the zero eigenvalue of Sec. II-B-1; b_i is its unit eigenvector and
-    lambda_i starts at the next eigenvalue (Sec. II-B-3, "minimum nonzero").
+    as the zero eigenvalue of Sec. II-B-1 (and set to zero in the R' that the
+    naive rule, the first-stage rule, the Wiener filter and the objective use);
+    b_i is its unit eigenvector and lambda_i starts at the next eigenvalue
+    (Sec. II-B-3, "minimum nonzero").
   * Real quantities formed from complex products (tau_aa, tau_xx, rho_aa,
     rho_xx, b^H R^u b, tr(.)) take the real part.
   * Update order inside one pass of the repeat loop follows Algorithms 1 and 2:
@@ -61,12 +63,17 @@ def setup(a, Rp, lambda0=None) -> Setup:
 
     b_i: unit eigenvector of R'_i for its zero eigenvalue.  (R')^+ from the
     eigendecomposition.  lambda_i: smallest nonzero eigenvalue unless given.
+    The returned R' has its smallest eigenvalue set to exactly zero, so that
+    R_i = R' + lambda b b^H and R_i^{-1} = (R')^+ + b b^H / lambda hold for any
+    Hermitian input (for a rank-(M-1) input this changes nothing).
     """
     a = np.asarray(a, np.complex128)
     Rp = np.asarray(Rp, np.complex128)
     Rp = 0.5 * (Rp + _herm(Rp))
     mu, E = np.linalg.eigh(Rp)                       # ascending, orthonormal columns
     b = E[:, :, 0]
+    # the smallest eigenvalue is the zero one: R' is used with it set to zero exactly
+    Rp = Rp - mu[:, 0, None, None] * np.einsum("im,in->imn", b, np.conj(b))
     En = E[:, :, 1:]
     Rp_pinv = np.einsum("imk,ik,ink->imn", En, 1.0 / mu[:, 1:], np.conj(En))
     lam0 = mu[:, 1].copy() if lambda0 is None else np.asarray(lambda0, np.float64).copy()
