@@ -93,6 +93,16 @@ typedef struct {
     int    persistent;       /* 1: the accelerated kernel runs as a persistent grid of
                                 resident CTAs that take rows (longest first) from an
                                 atomic counter; 0 (default): one CTA per row            */
+    int    ckpt_stride;      /* accelerated rule: k > 0 keeps the EM state entering every
+                                k-th pass since the last rcscm_setup / rcscm_set_state
+                                (a checkpoint) for rcscm_backward; 0 (default): none.
+                                With k > 0, block 0 picks 128 (J <= 512) or 256 (J <=
+                                2048), an explicit block must be 128 or 256, J <= 2048,
+                                and rcscm_graph_create is not available                 */
+    int    ckpt_max_iters;   /* with ckpt_stride > 0: most passes that may run between
+                                two rcscm_setup / rcscm_set_state calls; sizes the
+                                checkpoint memory, ceil(ckpt_max_iters / ckpt_stride)
+                                states of 8 B per slot                                   */
 } rcscm_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -185,6 +195,30 @@ int rcscm_autotune(rcscm_ctx* ctx, int n_iter_probe, int* chosen_block, int* cho
  * too. */
 int rcscm_graph_create(rcscm_ctx* ctx, int n_iter, void* h_out);
 int rcscm_graph_launch(rcscm_ctx* ctx, void* stream);
+
+/* Gradient of a real loss L of the Wiener estimate h (rcscm_extract with the
+ * current state) with respect to x, a and R', through the K accelerated passes
+ * run since the last rcscm_setup or rcscm_set_state, the Wiener filter, the
+ * per-slot invariants and the per-frequency setup.  The paper defines no
+ * gradient: this is reverse-mode differentiation of the computation of
+ * Algorithm 2 (Sec. III-C-2), the posterior mean (Sec. II-A) and the setup of
+ * Sec. II-B-1 / Eq. (eq:riinv).  Needs a context created with ckpt_stride > 0:
+ * the state entering each pass is recomputed from the nearest checkpoint with
+ * the forward kernel's code, bit for bit.  Per-slot adjoint arithmetic is FP32,
+ * per-frequency FP64.  lambda0 and the initial variances are held constant (no
+ * gradient flows into them, including the dependence of the default
+ * lambda0 = mu_2 on R').  Device buffers, utterances concatenated in context
+ * order:
+ *   grad_h  complex64  like h_out ([I][J][M] each): dL/dRe h + i dL/dIm h;
+ *   grad_x  complex64  like x ([I][J][M] each), same convention;
+ *   grad_a  complex128 [I][M] each;
+ *   grad_Rp complex128 [I][M][M] each: the gradient through the Hermitian part
+ *           (R' + R'^H)/2 that the setup reads, itself Hermitian; it is the
+ *           exact first-order gradient when the eigenvalues of R' are distinct.
+ * Every output element is written.  Errors: EINVAL (NULL buffer, no checkpoints,
+ * a block or row length the adjoint kernel does not support, passes run with a
+ * different block since the last setup), ECUDA. */
+int rcscm_backward(rcscm_ctx* ctx, const void* grad_h, void* grad_x, void* grad_a, void* grad_Rp, void* stream);
 
 /* One-shot solve of a single utterance from HOST memory: copies x, a, Rp, rh0,
  * ru0 (same layouts as rcscm_problem, host pointers; lambda0 may be NULL) to the

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librcscm.so")
-SOURCES = ["api.cu", "setup.cu", "iterate.cu", "naive.cu", "extract.cu", "objective.cu", "host.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "setup.cu", "iterate.cu", "naive.cu", "extract.cu", "objective.cu", "host.cu", "noalloc.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

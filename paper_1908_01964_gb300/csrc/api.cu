@@ -33,6 +33,13 @@ struct rcscm_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    // checkpoints for rcscm_backward (ckpt_stride > 0)
+    int n_ckpt = 0;
+    float* ckpt_rh = nullptr;        // [n_ckpt][S]
+    float* ckpt_ru = nullptr;        // [n_ckpt][S]
+    float* ckpt_lam = nullptr;       // [n_ckpt][R]
+    int iters_done = 0;              // passes since the last setup / set_state
+    int iter_block = 0;              // block of those passes (-1: mixed)
 };
 
 namespace {
@@ -77,6 +84,11 @@ int valid_options(const rcscm_options* o) {
     if (!accel_block_ok(o->block)) return 0;
     if (o->iters_per_launch < 0) return 0;
     if (o->persistent != 0 && o->persistent != 1) return 0;
+    if (o->ckpt_stride < 0) return 0;
+    if (o->ckpt_stride > 0) {
+        if (o->rule != RCSCM_RULE_ACCEL || o->ckpt_max_iters < 1) return 0;
+        if (o->block != 0 && o->block != 128 && o->block != 256) return 0;
+    }
     return 1;
 }
 
@@ -107,6 +119,8 @@ void rcscm_default_options(rcscm_options* opt) {
     opt->block = 0;
     opt->iters_per_launch = 0;
     opt->persistent = 0;
+    opt->ckpt_stride = 0;
+    opt->ckpt_max_iters = 0;
 }
 
 const char* rcscm_strerror(int code) {
@@ -144,10 +158,15 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
         max_j = std::max<int>(max_j, (int)q.J);
     }
     if (R > INT32_MAX || n_blocks > INT32_MAX) return RCSCM_EINVAL;
+    rcscm_options eff = *opt;
+    if (eff.ckpt_stride > 0) {               // the adjoint kernel's shapes: 128 x 4 or 256 x 8 slots
+        if (eff.block == 0) eff.block = adjoint_block(max_j);
+        if (eff.block == 0 || max_j > 8 * eff.block || (eff.block == 128 && max_j > 512)) return RCSCM_EINVAL;
+    }
 
     rcscm_ctx* c = new (std::nothrow) rcscm_ctx();
     if (!c) return RCSCM_ENOMEM;
-    c->opt = *opt;
+    c->opt = eff;
     c->probs.assign(probs, probs + n_probs);
     c->R = R;
     c->S = S;
@@ -158,7 +177,7 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
     std::vector<RowDesc> rows((size_t)R);
     std::vector<BlockMap> bmap((size_t)n_blocks);
     std::vector<int> jrow((size_t)R), mrow((size_t)R);
-    int64_t r = 0, s = 0, o = 0, sc = 0, b = 0;
+    int64_t r = 0, s = 0, o = 0, sc = 0, b = 0, ao = 0, po = 0;
     for (int p = 0; p < n_probs; ++p) {
         const rcscm_problem& q = probs[p];
         c->row0.push_back(r);
@@ -169,6 +188,8 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
             rd.slot_off = s;
             rd.out_off = o;
             rd.scratch_off = sc;
+            rd.a_off = ao;
+            rd.rp_off = po;
             rd.x = static_cast<const float2*>(q.x) + i * q.J * q.M;
             rd.a = static_cast<const double2*>(q.a) + i * q.M;
             rd.Rp = static_cast<const double2*>(q.Rp) + i * q.M * q.M;
@@ -185,6 +206,8 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
             s += q.J;
             o += q.J * q.M;
             sc += q.J * q.M * q.M;
+            ao += q.M;
+            po += q.M * q.M;
         }
     }
     std::vector<int> first_block;
@@ -242,6 +265,13 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
             cudaDeviceGetAttribute(&d.n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             st = RCSCM_ECUDA;
     }
+    if (!st && eff.ckpt_stride > 0) {
+        c->n_ckpt = (eff.ckpt_max_iters + eff.ckpt_stride - 1) / eff.ckpt_stride;
+        st = dalloc(c, &d.evec64, Rz * 64);
+        if (!st) st = dalloc(c, &c->ckpt_rh, Sz * (size_t)c->n_ckpt);
+        if (!st) st = dalloc(c, &c->ckpt_ru, Sz * (size_t)c->n_ckpt);
+        if (!st) st = dalloc(c, &c->ckpt_lam, Rz * (size_t)c->n_ckpt);
+    }
     if (!st && opt->rule == RCSCM_RULE_NAIVE) {
         float* q = nullptr;
         st = dalloc(c, &q, (size_t)naive_scratch);
@@ -280,6 +310,8 @@ int rcscm_setup(rcscm_ctx* c, void* stream) {
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_setup(c->d, (int)c->R, c->opt.null_tol, cs);
     if (e == cudaSuccess) e = launch_invariants(c->d, c->n_blocks, cs);
+    c->iters_done = 0;
+    c->iter_block = 0;
     return map_cuda(e);
 }
 
@@ -289,15 +321,34 @@ int rcscm_iterate(rcscm_ctx* c, int n_iter, void* stream) {
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     const IterParams p = iter_params(c->opt);
     const int chunk = c->opt.iters_per_launch > 0 ? c->opt.iters_per_launch : n_iter;
-    for (int done = 0; done < n_iter; done += chunk) {
-        const int k = std::min(chunk, n_iter - done);
-        cudaError_t e;
+    const int stride = c->opt.ckpt_stride;
+    if (stride > 0 && n_iter > c->opt.ckpt_max_iters - c->iters_done) return RCSCM_EINVAL;
+    for (int done = 0; done < n_iter;) {
+        int k = std::min(chunk, n_iter - done);
+        cudaError_t e = cudaSuccess;
+        if (stride > 0) {                    // launches end at checkpoint boundaries
+            const int u = c->iters_done;
+            k = std::min(k, stride - u % stride);
+            if (u % stride == 0) {
+                const size_t q = (size_t)(u / stride);
+                e = cudaMemcpyAsync(c->ckpt_rh + q * c->S, c->d.rh, c->S * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(c->ckpt_ru + q * c->S, c->d.ru, c->S * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(c->ckpt_lam + q * c->R, c->d.lam, c->R * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+                if (e != cudaSuccess) return map_cuda(e);
+            }
+        }
         if (c->opt.rule == RCSCM_RULE_ACCEL)
             e = launch_accel(c->d, (int)c->R, c->max_j, c->opt.block, k, p, c->opt.persistent != 0, cs);
         else
             e = launch_naive(c->d, c->naive_rows, c->count_by_m, c->first_by_m, k, p,
                              c->opt.rule == RCSCM_RULE_NAIVE_F64, cs);
         if (e != cudaSuccess) return map_cuda(e);
+        const int blk = c->opt.block;
+        c->iter_block = (c->iters_done == 0 || c->iter_block == blk) ? blk : -1;
+        c->iters_done += k;
+        done += k;
     }
     return RCSCM_OK;
 }
@@ -331,6 +382,8 @@ int rcscm_set_state(rcscm_ctx* c, int p, const float* rh, const float* ru, const
     if (ru && e == cudaSuccess) e = cudaMemcpyAsync(c->d.ru + c->slot0[(size_t)p], ru, n * sizeof(float), cudaMemcpyDeviceToDevice, cs);
     if (lambda && e == cudaSuccess)
         e = cudaMemcpyAsync(c->d.lam + c->row0[(size_t)p], lambda, (size_t)q.I * sizeof(float), cudaMemcpyDeviceToDevice, cs);
+    c->iters_done = 0;                       // the set state is the new starting point of the passes
+    c->iter_block = 0;
     return map_cuda(e);
 }
 
@@ -438,11 +491,13 @@ int rcscm_autotune(rcscm_ctx* c, int n_iter_probe, int* chosen_block, int* chose
     if (e == cudaSuccess) e = copy_state(true);
     const IterParams p = iter_params(c->opt);
     float best = 3.0e38f;
-    int best_block = accel_default_block(c->max_j), best_pers = 0;
+    const bool fixed_block = c->opt.ckpt_stride > 0;   // the adjoint needs the context's block
+    int best_block = fixed_block ? c->opt.block : accel_default_block(c->max_j), best_pers = 0;
     const int blocks[] = {32, 64, 128, 256, 512, 1024};
     for (int bi = 0; bi < 6 && e == cudaSuccess; ++bi) {
         const int b = blocks[bi];
         if ((int64_t)b * accel_max_spt(b) < c->max_j) continue;
+        if (fixed_block && b != c->opt.block) continue;
         for (int pers = 0; pers <= 1 && e == cudaSuccess; ++pers) {
             float t = 3.0e38f;
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
@@ -481,6 +536,7 @@ int rcscm_autotune(rcscm_ctx* c, int n_iter_probe, int* chosen_block, int* chose
 
 int rcscm_graph_create(rcscm_ctx* c, int n_iter, void* h_out) {
     if (!c || n_iter < 0 || !h_out) return RCSCM_EINVAL;
+    if (c->opt.ckpt_stride > 0) return RCSCM_EINVAL;   // checkpoint bookkeeping lives on the host
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
     c->gexec = nullptr;
@@ -502,6 +558,26 @@ int rcscm_graph_create(rcscm_ctx* c, int n_iter, void* h_out) {
     if (e2 != cudaSuccess) return map_cuda(e2);
     c->graph = g;
     return map_cuda(cudaGraphInstantiate(&c->gexec, g, 0));
+}
+
+int rcscm_backward(rcscm_ctx* c, const void* grad_h, void* grad_x, void* grad_a, void* grad_Rp, void* stream) {
+    if (!c || !grad_h || !grad_x || !grad_a || !grad_Rp) return RCSCM_EINVAL;
+    if (c->opt.ckpt_stride <= 0) return RCSCM_EINVAL;
+    if (c->iters_done > 0 && c->iter_block != c->opt.block) return RCSCM_EINVAL;
+    AdjointArgs g;
+    g.grad_h = static_cast<const float2*>(grad_h);
+    g.grad_x = static_cast<float2*>(grad_x);
+    g.grad_a = static_cast<double2*>(grad_a);
+    g.grad_Rp = static_cast<double2*>(grad_Rp);
+    g.ckpt_rh = c->ckpt_rh;
+    g.ckpt_ru = c->ckpt_ru;
+    g.ckpt_lam = c->ckpt_lam;
+    g.K = c->iters_done;
+    g.stride = c->opt.ckpt_stride;
+    g.S = c->S;
+    g.R = c->R;
+    return map_cuda(launch_adjoint(c->d, (int)c->R, c->max_j, c->opt.block, g, iter_params(c->opt),
+                                   static_cast<cudaStream_t>(stream)));
 }
 
 int rcscm_graph_launch(rcscm_ctx* c, void* stream) {

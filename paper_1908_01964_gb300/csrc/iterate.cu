@@ -30,163 +30,25 @@
 
 #include <algorithm>
 
-#include "rcscm_internal.cuh"
+#include "accel_common.cuh"
 
 namespace rcscm {
 namespace {
 
-// Sum over the block with one __syncthreads; `red` is double-buffered by the
-// pass parity so consecutive passes never race on it.  Every thread returns
-// the same, order-fixed value.  A single-warp block needs no shared memory.
-template <int BLOCK>
-__device__ __forceinline__ float block_sum(float v, float (*red)[BLOCK / 32 > 0 ? BLOCK / 32 : 1], int parity) {
-    constexpr int NW = BLOCK / 32;
-    v = warp_sum(v);
-    if constexpr (NW == 1) {
-        return v;
-    } else {
-        const int lane = threadIdx.x & 31;
-        if (lane == 0) red[parity][threadIdx.x >> 5] = v;
-        __syncthreads();
-        float t = red[parity][lane & (NW - 1)];
-#pragma unroll
-        for (int o = NW / 2; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        return t;
-    }
-}
-
-// 1/x for positive normal x: hardware approximation refined by one Newton step.
-__device__ __forceinline__ float rcp_refined(float x) {
-    const float r = rcp_approx(x);
-    return fmaf(r, fmaf(-x, r, 1.0f), r);
-}
-
-// ---- packed pairs of FP32 values (sm_100+ f32x2 instructions) ---------------------
-// Two slots are updated by one packed instruction: each half is an ordinary
-// IEEE FP32 operation, so results equal the scalar code bit for bit.
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pk(float lo, float hi) {
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float lo_of(f32x2 v) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return a;
-}
-__device__ __forceinline__ float hi_of(f32x2 v) {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return b;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f32x2 rcp2(f32x2 v) { return pk(rcp_approx(lo_of(v)), rcp_approx(hi_of(v))); }
-__device__ __forceinline__ f32x2 dup(float v) { return pk(v, v); }
-
-// One row with NP pairs of chunks (chunk k = slots k * BLOCK + threadIdx.x;
-// pair q = chunks 2q and 2q + 1), kept in registers for all n_iter passes.
-// Slots past the end of the row are padding that contributes exactly zero:
-// r_h = 0 and r_u = 1 throughout (their r_h offset beta/(alpha+2) is replaced by 0).
+// One row, all n_iter passes with the row held in registers (RowState).
 template <int BLOCK, int NP>
 __device__ __forceinline__ void accel_row(const DevState& d, int r, int J, int64_t off, const RowConst& c,
                                           int n_iter, const IterParams& p,
                                           float (*red)[BLOCK / 32 > 0 ? BLOCK / 32 : 1]) {
-    const int tid = threadIdx.x;
-    f32x2 tr[NP], ti[NP], sr[NP], si[NP], kapM[NP], rh[NP], ru[NP], B[NP];
-    float cb_lo = p.c_b, cb_hi = p.c_b;                       // r_h offset of the last pair
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        float v[2][6];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int j = (2 * q + h) * BLOCK + tid;
-            if (j < J) {
-                const float4 t = d.inv4[off + j];
-                v[h][0] = t.x; v[h][1] = t.y; v[h][2] = t.z; v[h][3] = t.w;
-                v[h][4] = fmaf(d.kap[off + j], c.invM, p.ru_floor);   // r_u >= ru_floor by construction
-                v[h][5] = d.rh[off + j];
-            } else {
-                v[h][0] = v[h][1] = v[h][2] = v[h][3] = 0.f;
-                v[h][4] = 1.f;                                       // padding keeps r_u = 1
-                v[h][5] = 0.f;
-                if (q == NP - 1) { if (h == 0) cb_lo = 0.f; else cb_hi = 0.f; }
-            }
-        }
-        tr[q] = pk(v[0][0], v[1][0]);
-        ti[q] = pk(v[0][1], v[1][1]);
-        sr[q] = pk(v[0][2], v[1][2]);
-        si[q] = pk(v[0][3], v[1][3]);
-        kapM[q] = pk(v[0][4], v[1][4]);
-        rh[q] = pk(v[0][5], v[1][5]);
-        const int j0 = 2 * q * BLOCK + tid, j1 = j0 + BLOCK;
-        ru[q] = pk(j0 < J ? d.ru[off + j0] : 1.f, j1 < J ? d.ru[off + j1] : 1.f);
-        B[q] = 0;
-    }
-
-    const f32x2 NSR = dup(-c.sab_re), NSI = dup(-c.sab_im), SI = dup(c.sab_im), SAB2 = dup(c.sab2);
-    const f32x2 NITAA = dup(-c.inv_taa), TAAM = dup(c.taaM), CA2 = dup(p.c_a2);
-    const f32x2 CB = dup(p.c_b), CB_LAST = pk(cb_lo, cb_hi);
-    float lam = d.lam[r];
-    const float invJ = 1.0f / (float)J;
-    for (int it = 0; it < n_iter; ++it) {
-        const float il = rcp_refined(lam);
-        const f32x2 RTAA = dup(fmaf(c.sab2, il, c.taa));          // rho~_aa, Eq. (eq:traa_accel)
-        const float slr = c.sab_re * il, sli = c.sab_im * il;
-        const f32x2 SLR = dup(slr), SLI = dup(sli), NSLI = dup(-sli);
-        f32x2 part = dup(0.f);
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            const f32x2 pr = fma2(SLR, sr[q], fma2(NSLI, si[q], tr[q]));
-            const f32x2 pi = fma2(SLR, si[q], fma2(SLI, sr[q], ti[q]));
-            const f32x2 g = mul2(rh[q], rcp2(fma2(rh[q], RTAA, ru[q])));
-            const f32x2 cr = mul2(g, pr), ci = mul2(g, pi);
-            const f32x2 Q = mul2(g, ru[q]);
-            const f32x2 rhat = fma2(ci, ci, fma2(cr, cr, Q));
-            const f32x2 dr = fma2(cr, NSR, fma2(ci, NSI, sr[q]));
-            const f32x2 di = fma2(ci, NSR, fma2(cr, SI, si[q]));
-            const f32x2 Bk = fma2(dr, dr, fma2(di, di, mul2(Q, SAB2)));
-            part = fma2(Bk, rcp2(ru[q]), part);
-            const f32x2 er = fma2(tr[q], NITAA, cr);
-            const f32x2 ei = fma2(ti[q], NITAA, ci);
-            ru[q] = fma2(TAAM, fma2(er, er, fma2(ei, ei, Q)), kapM[q]);    // A / M
-            B[q] = Bk;
-            rh[q] = fma2(rhat, CA2, q == NP - 1 ? CB_LAST : CB);
-        }
-        lam = block_sum<BLOCK>(lo_of(part) + hi_of(part), red, it & 1) * invJ;
-        const f32x2 ILM = dup(rcp_refined(lam) * c.invM);
-#pragma unroll
-        for (int q = 0; q < NP; ++q) ru[q] = fma2(B[q], ILM, ru[q]);
-    }
-
-    bool clamp = false;
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int j = (2 * q + h) * BLOCK + tid;
-            if (j < J) {
-                const float rhv = h ? hi_of(rh[q]) : lo_of(rh[q]);
-                const float ruv = h ? hi_of(ru[q]) : lo_of(ru[q]);
-                d.rh[off + j] = rhv;
-                d.ru[off + j] = ruv;
-                clamp |= (n_iter > 0) && (ruv <= p.ru_floor);
-            }
-        }
-    }
-    if (clamp) atomicOr(d.status, kFlagClamp);
-    if (tid == 0) {
-        d.lam[r] = lam;
-        if (!(lam > 0.f) || !(lam <= FLT_MAX)) atomicOr(d.status, kFlagNonfinite);
+    RowState<BLOCK, NP> st;
+    st.load_inv(d, off, J, c, p);
+    st.load_state(d.rh + off, d.ru + off, d.lam[r]);
+    for (int it = 0; it < n_iter; ++it) st.pass(c, p, red, it & 1);
+    st.store_state(d.rh + off, d.ru + off);
+    if (n_iter > 0 && st.any_clamp(p.ru_floor)) atomicOr(d.status, kFlagClamp);
+    if (threadIdx.x == 0) {
+        d.lam[r] = st.lam;
+        if (!(st.lam > 0.f) || !(st.lam <= FLT_MAX)) atomicOr(d.status, kFlagNonfinite);
     }
 }
 

@@ -141,16 +141,6 @@ __global__ void __launch_bounds__(kNaiveBlock) naive_kernel(DevState d, const in
     const int tid = threadIdx.x;
     const T c_a2 = kF64 ? T(p.c_a2_f64) : T(p.c_a2);
     const T c_b = kF64 ? T(p.c_b_f64) : T(p.c_b);
-    for (int e = tid; e < M * M; e += kNaiveBlock) {
-        const int m = e / M, n = e % M;
-        if constexpr (kF64) {
-            const double2 amn = rd->Rp[m * M + n], anm = rd->Rp[n * M + m];
-            sRp[m][n] = cx(0.5 * (amn.x + anm.x), 0.5 * (amn.y - anm.y));
-        } else {
-            const float2 v = d.rp32[(size_t)r * 64 + e];
-            sRp[m][n] = cx(v.x, v.y);
-        }
-    }
     if (tid < M) {
         if constexpr (kF64) {
             const double2 av = rd->a[tid], bv = d.b64[(size_t)r * kMaxM + tid];
@@ -160,6 +150,19 @@ __global__ void __launch_bounds__(kNaiveBlock) naive_kernel(DevState d, const in
             const float2 av = d.a32[(size_t)r * kMaxM + tid], bv = d.b32[(size_t)r * kMaxM + tid];
             sa[tid] = cx(av.x, av.y);
             sb[tid] = cx(bv.x, bv.y);
+        }
+    }
+    __syncthreads();
+    // R' with its smallest eigenvalue set to zero (so R' + lambda b b^H is the model's R_i)
+    for (int e = tid; e < M * M; e += kNaiveBlock) {
+        const int m = e / M, n = e % M;
+        if constexpr (kF64) {
+            const double2 amn = rd->Rp[m * M + n], anm = rd->Rp[n * M + m];
+            const double mu1 = d.mu[(size_t)r * kMaxM];
+            sRp[m][n] = cx(0.5 * (amn.x + anm.x), 0.5 * (amn.y - anm.y)) - (sb[m] * conj(sb[n])) * mu1;
+        } else {
+            const float2 v = d.rp32[(size_t)r * 64 + e];
+            sRp[m][n] = cx(v.x, v.y);
         }
     }
     T lam = T(d.lam[r]);

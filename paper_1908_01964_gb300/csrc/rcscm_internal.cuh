@@ -22,6 +22,8 @@ struct RowDesc {
     int64_t slot_off;       // first slot of the row in the per-slot arrays
     int64_t out_off;        // first complex element of the row in the concatenated h_out
     int64_t scratch_off;    // naive rule: first float of the row's R^u scratch
+    int64_t a_off;          // first element of the row in concatenated [I][M] arrays (grad_a)
+    int64_t rp_off;         // first element of the row in concatenated [I][M][M] arrays (grad_Rp)
     const float2* x;        // row start in the caller's x  (J x M complex64)
     const double2* a;       // caller's a_i                 (M complex128)
     const double2* Rp;      // caller's R'_i                (M x M complex128)
@@ -66,6 +68,7 @@ struct DevState {
     float2* a32;           // [R][8]
     float2* b32;           // [R][8]
     float2* rp32;          // [R][8][8]  (naive rule)
+    double2* evec64;       // [R][64] eigenvectors of R', entry m * M + i = e_i[m], ascending (adjoint), or nullptr
     // per-slot invariants and EM state
     float4* inv4;          // [S] {tau_ax.re, tau_ax.im, sigma_bx.re, sigma_bx.im}
     float* kap;            // [S] kappa = tau_xx - |tau_ax|^2 / tau_aa
@@ -154,6 +157,22 @@ inline bool accel_block_ok(int block) {
     return block == 0 || block == 32 || block == 64 || block == 128 || block == 256 || block == 512 || block == 1024;
 }
 inline int accel_max_j(int block) { return block ? block * accel_max_spt(block) : 512 * 8; }
+// Block of the adjoint kernel (and of the forward kernel of a context that keeps
+// checkpoints): 128 threads for rows up to 512 frames, 256 up to 2048; 0 beyond.
+inline int adjoint_block(int max_j) { return max_j <= 512 ? 128 : (max_j <= 2048 ? 256 : 0); }
+
+struct AdjointArgs {
+    const float2* grad_h;   // upstream gradient of h (concatenated, like h_out)
+    float2* grad_x;         // like x, concatenated
+    double2* grad_a;        // [rows][M] concatenated
+    double2* grad_Rp;       // [rows][M][M] concatenated
+    const float* ckpt_rh;   // [n_ckpt][S]: state entering pass k * stride
+    const float* ckpt_ru;
+    const float* ckpt_lam;  // [n_ckpt][R]
+    int K;                  // passes run since setup
+    int stride;             // passes between checkpoints
+    int64_t S, R;
+};
 
 // Launchers (defined in the .cu files, called by the C ABI in api.cu).
 namespace rcscm {
@@ -172,4 +191,6 @@ cudaError_t launch_objective(const DevState& d, int n_blocks, const IterParams& 
 cudaError_t launch_naive(const DevState& d, const int* rows_by_m, const int* count_by_m,
                          const int* first_by_m, int n_iter, const IterParams& p, bool f64, cudaStream_t s);
 cudaError_t launch_extract(const DevState& d, int n_blocks, float2* h_out, cudaStream_t s);
+cudaError_t launch_adjoint(const DevState& d, int n_rows, int max_j, int block, const AdjointArgs& a,
+                           const IterParams& p, cudaStream_t s);
 }  // namespace rcscm

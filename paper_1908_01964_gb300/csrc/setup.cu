@@ -182,7 +182,6 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
         const float2 hf = make_float2((float)h.x, (float)h.y);
         A32[m][n] = hf;
         V32[m][n] = make_float2(m == n ? 1.f : 0.f, 0.f);
-        d.rp32[(size_t)r * 64 + e] = hf;
     }
     if (l < M) {
         const double2 av = rd.a[l];
@@ -301,6 +300,8 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
         d.b64[(size_t)r * kMaxM + l] = bv;
         d.b32[(size_t)r * kMaxM + l] = make_float2((float)bv.x, (float)bv.y);
     }
+    if (d.evec64)                              // eigenbasis for the adjoint
+        for (int e = l; e < MM; e += kGroupLanes) d.evec64[(size_t)r * 64 + e] = X[e / M][perm[e % M]];
     // c_i = e_i^H a and 1/sqrt(mu_i) for the nonzero eigenpairs (sorted index i = 1..M-1)
     if (l >= 1 && l < M) {
         const int kk = perm[l];
@@ -329,6 +330,13 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     // w = u - alpha e_0 with alpha = -ph0 |u| -> w_0 = ph0 (|u_0| + 1); |w|^2 = 2 + 2|u_0|
     const double two_over_wn2 = 2.0 / (2.0 + 2.0 * au0);
 
+    // FP32 copy of R' for the naive rule, with the smallest eigenvalue set to zero
+    // (R' + lambda b b^H is then exactly the model's R_i)
+    for (int e = l; e < MM; e += kGroupLanes) {
+        const int m = e / M, n = e % M;
+        const double2 v = zsub(A[m][n], zscale(zmulc(X[n][k0], X[m][k0]), mu1));
+        d.rp32[(size_t)r * 64 + e] = make_float2((float)v.x, (float)v.y);
+    }
     // Phi entries (kk, n): row 0 (R'^+ a)^H, rows 1..M-2 H L^H, row M-1 b^H
     float2* phi = d.phi + (size_t)r * 64;
     for (int e = l; e < MM; e += kGroupLanes) {

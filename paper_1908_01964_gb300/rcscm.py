@@ -36,7 +36,8 @@ class Problem(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("rule", c_int), ("alpha", c_double), ("beta", c_double),
                 ("ru_floor", c_float), ("null_tol", c_double), ("block", c_int),
-                ("iters_per_launch", c_int), ("persistent", c_int)]
+                ("iters_per_launch", c_int), ("persistent", c_int),
+                ("ckpt_stride", c_int), ("ckpt_max_iters", c_int)]
 
 
 class RcscmError(RuntimeError):
@@ -86,6 +87,7 @@ def lib():
         "rcscm_autotune": (c_int, [vp, c_int, POINTER(c_int), POINTER(c_int), vp]),
         "rcscm_graph_create": (c_int, [vp, c_int, vp]),
         "rcscm_graph_launch": (c_int, [vp, vp]),
+        "rcscm_backward": (c_int, [vp, vp, vp, vp, vp, vp]),
         "rcscm_host_create": (c_int, [POINTER(vp), c_int64, c_int64, c_int64, POINTER(Options), c_int]),
         "rcscm_host_run": (c_int, [vp, vp, vp, vp, vp, vp, vp, c_int, vp, vp, vp, vp]),
         "rcscm_host_destroy": (None, [vp]),
@@ -109,12 +111,14 @@ def _check(code: int, where: str, allow=(OK,)):
 
 
 def options(rule: str = "accel", alpha: float = 1.1, beta: float = 1e-16, ru_floor: float = FLT_MIN,
-            null_tol: float = 1e-6, block: int = 0, iters_per_launch: int = 0, persistent: int = 0) -> Options:
+            null_tol: float = 1e-6, block: int = 0, iters_per_launch: int = 0, persistent: int = 0,
+            ckpt_stride: int = 0, ckpt_max_iters: int = 0) -> Options:
     o = Options()
     lib().rcscm_default_options(ctypes.byref(o))
     o.rule = {"accel": RULE_ACCEL, "naive": RULE_NAIVE, "naive64": RULE_NAIVE_F64}[rule]
     o.alpha, o.beta, o.ru_floor, o.null_tol = alpha, beta, ru_floor, null_tol
     o.block, o.iters_per_launch, o.persistent = block, iters_per_launch, int(persistent)
+    o.ckpt_stride, o.ckpt_max_iters = int(ckpt_stride), int(ckpt_max_iters)
     return o
 
 
@@ -282,6 +286,34 @@ class Solver:
             raise ValueError("out must be a contiguous complex64 tensor with one element per output")
         self._graph_out = out
         _check(lib().rcscm_graph_create(self.ctx, int(n_iter), c_void_p(out.data_ptr())), "rcscm_graph_create")
+
+    def backward(self, grad_h, stream=None):
+        """Gradients of a real loss of extract()'s output (grad_h: complex64, one
+        element per output, dL/dRe h + i dL/dIm h) with respect to x, a and R',
+        through the passes run since setup.  Returns flat concatenations
+        (grad_x complex64 like the outputs, grad_a complex128 [sum I*M],
+        grad_Rp complex128 [sum I*M*M]); split_grads() gives per-utterance views.
+        Needs a Solver created with ckpt_stride > 0."""
+        import torch
+        if grad_h.dtype != torch.complex64 or grad_h.numel() != self.out_elements or not grad_h.is_contiguous():
+            raise ValueError("grad_h must be a contiguous complex64 tensor with one element per output")
+        kw = dict(device=self.device)
+        gx = torch.empty(self.out_elements, dtype=torch.complex64, **kw)
+        ga = torch.empty(int(sum(I * M for I, _, M in self.shapes)), dtype=torch.complex128, **kw)
+        gR = torch.empty(int(sum(I * M * M for I, _, M in self.shapes)), dtype=torch.complex128, **kw)
+        _check(lib().rcscm_backward(self.ctx, c_void_p(grad_h.data_ptr()), c_void_p(gx.data_ptr()),
+                                    c_void_p(ga.data_ptr()), c_void_p(gR.data_ptr()), _stream(stream)),
+               "rcscm_backward")
+        return gx, ga, gR
+
+    def split_grads(self, gx, ga, gR):
+        """Per-utterance views ([I,J,M], [I,M], [I,M,M]) of backward()'s results."""
+        out, ox, oa, orp = [], 0, 0, 0
+        for I, J, M in self.shapes:
+            out.append((gx[ox:ox + I * J * M].view(I, J, M), ga[oa:oa + I * M].view(I, M),
+                        gR[orp:orp + I * M * M].view(I, M, M)))
+            ox, oa, orp = ox + I * J * M, oa + I * M, orp + I * M * M
+        return out
 
     def graph_launch(self, stream=None):
         _check(lib().rcscm_graph_launch(self.ctx, _stream(stream)), "rcscm_graph_launch")
