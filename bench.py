@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="single-m4")
     ap.add_argument("--rule", choices=["accel", "naive"], default="accel")
+    ap.add_argument("--path", choices=["fused", "separate"], default="fused",
+                    help="fused: rcscm_setup_freq + rcscm_run (2 launches); separate: setup, iterate, extract")
     ap.add_argument("--iters-per-launch", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--persistent", type=int, default=0)
@@ -66,6 +68,14 @@ def parse():
     ap.add_argument("--clock-preroll", type=float, default=1.5, help="seconds of load before the timed region")
     ap.add_argument("--e2e-chunks", type=int, default=4, help="row chunks of the host pipeline")
     ap.add_argument("--json-out", default=None)
+    ap.add_argument("--replicas", type=int, default=1,
+                    help="solve R copies of the workload in one context (inputs shared, state per copy)")
+    ap.add_argument("--no-streaming", action="store_true", help="skip the streaming-mode HBM roofline section")
+    ap.add_argument("--streaming-replicas", type=int, default=8)
+    ap.add_argument("--streaming-launches", type=int, default=50)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the forward + adjoint section")
+    ap.add_argument("--adjoint-workload", default="adjoint-16")
+    ap.add_argument("--adjoint-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -140,6 +150,38 @@ def load_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         return {}
+
+
+# Kernel sources whose hash a profile summary records: a traffic figure is used
+# only while the kernel it was measured on is unchanged.
+KERNEL_SOURCES = {
+    "accel_kernel": ["accel_common.cuh", "iterate.cu", "rcscm_internal.cuh"],
+    "solve_kernel": ["accel_common.cuh", "iterate.cu", "rcscm_internal.cuh"],
+    "adjoint_kernel": ["accel_common.cuh", "adjoint.cu", "rcscm_internal.cuh"],
+}
+
+
+def kernel_source_hash(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1908_01964_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, case):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) that a
+    profiles/*.md summary records for `kernel` on `case`, if its source hash matches."""
+    import glob
+    import re
+    want = kernel_source_hash(kernel)
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            m = re.match(r"^traffic: kernel=(\S+) case=(\S+) bytes_per_launch=([0-9.eE+]+) source=(\w+)", line.strip())
+            if m and m.group(1) == kernel and m.group(2) == case and m.group(4) == want:
+                return float(m.group(3)), os.path.relpath(path, ROOT)
+    return None, None
 
 
 def dist_env():
@@ -217,34 +259,31 @@ def cpu_baseline(p, wl, rule):
 
 # ----------------------------------------------------------------------------- our arm
 
-def time_steps(solver, h, n_iter, K, W, flush, stream, sampler=None, preroll_s=0.0, graph=False):
+def time_steps(solver, h, n_iter, K, W, flush, stream, sampler=None, preroll_s=0.0, graph=False, fused=False):
+    """Returns (one, names): one(record) runs a step and, if record, returns its
+    CUDA events (start, then one per segment in `names`)."""
     import torch
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     if graph:
         solver.graph_create(n_iter, h)
+        names = ("step_graph",)
+        calls = (lambda: solver.graph_launch(),)
+    elif fused:
+        names = ("setup_freq", "run")
+        calls = (lambda: solver.setup_freq(), lambda: solver.run(n_iter, h))
+    else:
+        names = ("setup", "iterate", "extract")
+        calls = (lambda: solver.setup(), lambda: solver.iterate(n_iter), lambda: solver.extract(out=h))
 
     def one(record):
         flush.zero_()
-        e = [ev() for _ in range(4)] if record else None
-        if graph:                       # the whole step is one graph launch: no per-segment split
-            if record:
-                e[0].record(stream)
-            solver.graph_launch()
-            if record:
-                for k in (1, 2, 3):
-                    e[k].record(stream)
-            return e
+        e = [ev() for _ in range(len(calls) + 1)] if record else None
         if record:
             e[0].record(stream)
-        solver.setup()
-        if record:
-            e[1].record(stream)
-        solver.iterate(n_iter)
-        if record:
-            e[2].record(stream)
-        solver.extract(out=h)
-        if record:
-            e[3].record(stream)
+        for k, call in enumerate(calls):
+            call()
+            if record:
+                e[k + 1].record(stream)
         return e
 
     for _ in range(W):
@@ -256,7 +295,18 @@ def time_steps(solver, h, n_iter, K, W, flush, stream, sampler=None, preroll_s=0
             for _ in range(8):
                 one(False)
             torch.cuda.synchronize()
-    return one
+    return one, names
+
+
+def fused_ops_per_launch(specs, n_iter):
+    """FP32 lane-ops of one fused launch: per slot, 26 per pass, the projection
+    Phi x (8M + (M-2)(4M+3) + 1) and the Wiener filter (12 + 4M)."""
+    tot = 0
+    for sp in specs:
+        M = sp.M
+        per_slot = ACCEL_FP32_OPS_PER_SLOT_ITER * n_iter + 8 * M + (M - 2) * (4 * M + 3) + 1 + 12 + 4 * M
+        tot += sp.I * sp.J * per_slot
+    return tot
 
 
 def run_ours(args):
@@ -279,6 +329,9 @@ def run_ours(args):
     n_iter = wl.n_iter
     slots = wl.slots
     dprobs = [R.to_device(p, dev) for p in probs]
+    if args.replicas > 1:               # copies share the input tensors; each keeps its own state
+        dprobs = dprobs * args.replicas
+        slots *= args.replicas
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     peaks = load_peaks()
@@ -298,8 +351,9 @@ def run_ours(args):
     sampler = ClockSampler(torch.cuda.current_device() if ws == 1 else local) if rank == 0 or ws == 1 else None
     if sampler:
         sampler.wait_first()
-    one = time_steps(solver, h, n_iter, args.steps, args.warmup, flush, stream, sampler, args.clock_preroll,
-                     graph=args.graph)
+    fused = (args.path == "fused" and args.rule == "accel" and args.iters_per_launch == 0)
+    one, seg_names = time_steps(solver, h, n_iter, args.steps, args.warmup, flush, stream, sampler,
+                                args.clock_preroll, graph=args.graph, fused=fused)
     barrier()
     torch.cuda.synchronize()
     if sampler:
@@ -313,8 +367,8 @@ def run_ours(args):
     code = solver.status()
     if code not in (R.OK, R.ECLAMP):
         raise RuntimeError(f"device status after the timed steps: {R.strerror(code)}")
-    step_ms = [e[0].elapsed_time(e[3]) for e in events]
-    seg = {k: [e[i].elapsed_time(e[i + 1]) for e in events] for i, k in enumerate(("setup", "iterate", "extract"))}
+    step_ms = [e[0].elapsed_time(e[-1]) for e in events]
+    seg = {k: [e[i].elapsed_time(e[i + 1]) for e in events] for i, k in enumerate(seg_names)}
     total_ms = sum(step_ms)
     if ws > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
@@ -322,7 +376,10 @@ def run_ours(args):
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
     value = ws * slots * n_iter / (ms_per_step / 1e3)
-    it_ms = statistics.mean(seg["iterate"]) if not args.graph else None
+    if args.graph:
+        it_ms = None
+    else:
+        it_ms = statistics.mean(seg["run"] if fused else seg["iterate"])
     launches_per_iterate = 1 if args.iters_per_launch == 0 else -(-n_iter // args.iters_per_launch)
     if it_ms is None:                   # graph: time the accelerated kernel alone once, outside the steps
         tk = []
@@ -339,12 +396,28 @@ def run_ours(args):
     iters_per_launch = n_iter if args.iters_per_launch == 0 else args.iters_per_launch
 
     clocks = sampler.summary() if sampler else None
-    if args.rule == "accel" and args.iters_per_launch == 0:
+    if fused and not args.graph:
+        ops = fused_ops_per_launch(wl.specs, n_iter) * args.replicas
+        achieved = ops / (launch_ms / 1e3) / 1e9
+        peak = GB300_SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+        traffic, tsrc = profiled_traffic("solve_kernel", f"{wl.name}-x{args.replicas}")
+        m_bytes = sum(sp.I * sp.J * (16 * sp.M + 36) for sp in wl.specs) * args.replicas
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (FP32 lane-ops)",
+                    "frac": achieved / peak, "traffic": traffic, "traffic_source": tsrc,
+                    "traffic_algorithmic": m_bytes,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz max SM clock",
+                    "kernel": "solve_kernel (invariants from x, all passes in registers, Wiener output; one launch)",
+                    "algorithmic": (f"{ACCEL_FP32_OPS_PER_SLOT_ITER} FP32 ops + 2 MUFU per slot-pass, plus the "
+                                    "projection and the Wiener filter once per slot (f32x2 counts 2)"),
+                    "hbm_gbs_algorithmic": m_bytes / (launch_ms / 1e3) / 1e9}
+    elif args.rule == "accel" and args.iters_per_launch == 0:
         ops = ACCEL_FP32_OPS_PER_SLOT_ITER * slots * iters_per_launch
         achieved = ops / (launch_ms / 1e3) / 1e9
         peak = GB300_SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+        traffic, tsrc = profiled_traffic("accel_kernel", f"{wl.name}-x{args.replicas}-resident")
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (FP32 lane-ops)",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": traffic, "traffic_source": tsrc,
+                    "traffic_algorithmic": ACCEL_BYTES_PER_SLOT_LAUNCH * slots,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz max SM clock",
                     "kernel": "accel_kernel (register-resident, all iterations in one launch)",
                     "algorithmic": f"{ACCEL_FP32_OPS_PER_SLOT_ITER} FP32 ops + 2 MUFU per slot-iteration (f32x2 counts 2)",
@@ -353,8 +426,10 @@ def run_ours(args):
         bytes_ = ACCEL_BYTES_PER_SLOT_LAUNCH * slots
         achieved = bytes_ / (launch_ms / 1e3) / 1e9
         peak = float(peaks.get("hbm_gbs", 6800.0))
+        traffic, tsrc = profiled_traffic("accel_kernel", f"{wl.name}-x{args.replicas}-streaming")
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
+                    "traffic": traffic, "traffic_source": tsrc, "traffic_algorithmic": bytes_,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
                     "kernel": f"accel_kernel (streaming, {iters_per_launch} iteration(s) per launch)",
                     "algorithmic": f"{ACCEL_BYTES_PER_SLOT_LAUNCH} B per slot per launch"}
     else:
@@ -365,20 +440,24 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": DATA, "impl": "ours",
-        "config": {"workload": wl.name, "utterances": len(probs), "slots": slots, "n_iter": n_iter,
+        "config": {"workload": wl.name + (f" x{args.replicas}" if args.replicas > 1 else ""),
+                   "utterances": len(dprobs), "slots": slots, "n_iter": n_iter,
                    "M": sorted({s.M for s in wl.specs}), "I": sorted({s.I for s in wl.specs}),
                    "J": [min(s.J for s in wl.specs), max(s.J for s in wl.specs)], "rule": args.rule,
                    "iters_per_launch": args.iters_per_launch,
                    "block": tuned[0] if tuned else solver.opt.block,
                    "persistent": tuned[1] if tuned else solver.opt.persistent, "autotuned": tuned is not None,
                    "cuda_graph": args.graph,
+                   "path": "fused (rcscm_setup_freq + rcscm_run)" if fused else "separate (setup, iterate, extract)",
                    "step": "setup + invariants + n_iter EM passes + Wiener extraction, inputs resident in HBM",
                    "l2": "flushed between timed steps (256 MB write outside the step's event brackets)",
                    "parallelism": f"replicas x{ws} (one utterance set per GPU, no collective)"},
         "kernels_ms": ({k: statistics.mean(v) for k, v in seg.items()} if not args.graph
                        else {"step_graph": ms_per_step, "iterate_alone": it_ms}),
+        "launches_per_step": (1 + 1 + (1 if args.persistent else 0)) if fused else (2 + launches_per_iterate + 1),
         "roofline": roofline,
-        "gpu_launches": args.steps * (2 + launches_per_iterate + 1),
+        "gpu_launches": args.steps * ((2 + (1 if args.persistent else 0)) if fused
+                                      else (2 + launches_per_iterate * (2 if args.persistent else 1) + 1)),
         "objective_after_step": float(solver.objective().sum()),
         "clocks": clocks,
     }
@@ -388,7 +467,7 @@ def run_ours(args):
         kn = args.naive_steps if args.naive_steps is not None else min(args.steps, 10)
         for key, rule, k_steps in (("naive", "naive", kn), ("naive_f64", "naive64", max(1, min(kn, 3)))):
             nsolver = R.Solver(dprobs, rule=rule)
-            none = time_steps(nsolver, h, n_iter, k_steps, 1, flush, stream)
+            none, _ = time_steps(nsolver, h, n_iter, k_steps, 1, flush, stream)
             barrier()
             torch.cuda.synchronize()
             nev = [none(True) for _ in range(k_steps)]
@@ -405,8 +484,16 @@ def run_ours(args):
         result["naive"]["paper"] = ("87x: second-stage vs naive per iteration, MATLAB R2019a FP64 on an "
                                     "Intel Core i9-7900X, M=4, I=513, J~275")
 
+    # ---------------- streaming mode: one pass per launch over a working set larger than L2
+    if not args.no_streaming and args.rule == "accel":
+        result["streaming"] = streaming_roofline(dprobs[:len(probs)], args, R, peaks, stream)
+
+    # ---------------- adjoint (forward with checkpoints + rcscm_backward)
+    if not args.no_adjoint and args.rule == "accel":
+        result["adjoint"] = adjoint_section(args, R, dev, stream)
+
     # ---------------- end to end through the C ABI with host buffers
-    if not args.no_e2e and len(probs) == 1:
+    if not args.no_e2e and len(probs) == 1 and args.replicas == 1:
         result["e2e"] = e2e_host(probs[0], n_iter, args, R, n_chunks=args.e2e_chunks)
         result["e2e_oneshot"] = e2e_oneshot(probs[0], n_iter, args, R)
     elif not args.no_e2e:
@@ -417,6 +504,84 @@ def run_ours(args):
         result["cpu_baseline"] = cpu_baseline(probs[0], wl, args.rule)
     solver.close()
     return result if rank == 0 else None
+
+
+def streaming_roofline(dprobs, args, R, peaks, stream):
+    """HBM roofline of the accelerated kernel run one pass per launch (state
+    streamed through HBM each pass) on copies of the workload whose invariants
+    + state exceed L2: 36 algorithmic bytes per slot per launch."""
+    import torch
+    copies = dprobs * args.streaming_replicas
+    s = R.Solver(copies, rule="accel", iters_per_launch=1, block=args.block)
+    slots = s.info()["slots"]
+    s.setup()
+    for _ in range(5):
+        s.iterate(1)
+    n = args.streaming_launches
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(n):
+        s.iterate(1)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    code = s.status()
+    s.close()
+    ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(n)]
+    t = statistics.median(ms)
+    bytes_ = ACCEL_BYTES_PER_SLOT_LAUNCH * slots
+    achieved = bytes_ / (t / 1e3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic, tsrc = profiled_traffic("accel_kernel", f"{args.workload}-x{args.streaming_replicas}-streaming")
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "traffic_source": tsrc, "traffic_algorithmic": bytes_,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured burst copy)" if peaks else "fallback 6800 GB/s",
+            "kernel": "accel_kernel, 1 pass per launch",
+            "workload": f"{args.streaming_replicas} copies of the bench workload in one context, {slots} slots, "
+                        f"{bytes_ / 1e6:.0f} MB per launch (invariants + state > L2)",
+            "launch_us_median": 1e3 * t, "launches": n, "slot_updates_per_s": slots / (t / 1e3),
+            "status": R.strerror(code)}
+
+
+def adjoint_section(args, R, dev, stream):
+    """Forward (setup, K passes keeping checkpoints, Wiener) and rcscm_backward on
+    the adjoint workload; upstream gradient g_h = h (loss |h|^2 / 2)."""
+    import torch
+    wl, probs = make_inputs(args.adjoint_workload)
+    dprobs = [R.to_device(p, dev) for p in probs]
+    K = wl.n_iter
+    stride = int(wl.extra.get("ckpt_stride", 5))
+    s = R.Solver(dprobs, rule="accel", ckpt_stride=stride, ckpt_max_iters=K)
+    slots = s.info()["slots"]
+    h = torch.empty(s.out_elements, dtype=torch.complex64, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(record):
+        e = [ev() for _ in range(3)] if record else None
+        if record:
+            e[0].record(stream)
+        s.setup()
+        s.iterate(K)
+        s.extract(out=h)
+        if record:
+            e[1].record(stream)
+        g = s.backward(h)
+        if record:
+            e[2].record(stream)
+        return e, g
+    for _ in range(3):
+        step(False)
+    torch.cuda.synchronize()
+    rec = [step(True) for _ in range(args.adjoint_steps)]
+    torch.cuda.synchronize()
+    fwd = statistics.median(e[0].elapsed_time(e[1]) for e, _ in rec)
+    bwd = statistics.median(e[1].elapsed_time(e[2]) for e, _ in rec)
+    finite = all(bool(torch.isfinite(torch.view_as_real(t)).all()) for t in rec[-1][1])
+    s.close()
+    return {"workload": wl.name, "utterances": len(probs), "slots": slots, "K": K, "ckpt_stride": stride,
+            "forward_ms": fwd, "backward_ms": bwd, "backward_over_forward": bwd / fwd,
+            "value": slots * K / ((fwd + bwd) / 1e3), "unit": "differentiated slot-updates/s (forward + backward)",
+            "grads_finite": finite, "steps": args.adjoint_steps}
 
 
 def e2e_host(p, n_iter, args, R, n_chunks=4):

@@ -141,6 +141,23 @@ int rcscm_iterate(rcscm_ctx* ctx, int n_iter, void* stream);
  * h_out: device complex64, the utterances concatenated in order, each [I][J][M]. */
 int rcscm_extract(rcscm_ctx* ctx, void* h_out, void* stream);
 
+/* The same work as rcscm_setup + rcscm_iterate(n_iter) + rcscm_extract(h_out),
+ * in fewer launches.  rcscm_setup_freq runs the per-frequency part of
+ * rcscm_setup alone (eigendecomposition, b, (R')^+, lambda_0, tau_aa, sigma_ab,
+ * projection; Sec. II-B-1, Eq. (eq:riinv)).  rcscm_run then computes in ONE
+ * kernel per row, from the initial state (rh0, ru0, lambda_0) whatever ran
+ * before: the per-slot invariants from x (stored in the context, as rcscm_setup
+ * does), n_iter passes of Algorithm 2 in registers, and the Wiener output h_out;
+ * x is read once and the invariants and state are not re-read.  It needs the
+ * accelerated rule, iters_per_launch = 0 and no checkpoints (else EINVAL), and
+ * rcscm_setup_freq or rcscm_setup since the inputs last changed.  rcscm_solve =
+ * rcscm_setup_freq + rcscm_run, or the three separate calls in any other
+ * configuration.  Outputs, state and invariants are bitwise those of the
+ * separate calls. */
+int rcscm_setup_freq(rcscm_ctx* ctx, void* stream);
+int rcscm_run(rcscm_ctx* ctx, int n_iter, void* h_out, void* stream);
+int rcscm_solve(rcscm_ctx* ctx, int n_iter, void* h_out, void* stream);
+
 /* Copy one utterance's state out of / into the context (device pointers:
  * rh, ru [I][J] float, lambda [I] float).  set_state accepts any of them NULL
  * (left unchanged).  Errors: EINVAL for a bad index. */
@@ -188,8 +205,8 @@ int rcscm_objective(rcscm_ctx* ctx, double* value, void* stream);
  * EINVAL for a naive-rule context. */
 int rcscm_autotune(rcscm_ctx* ctx, int n_iter_probe, int* chosen_block, int* chosen_persistent, void* stream);
 
-/* Capture one full solve step -- rcscm_setup, rcscm_iterate(n_iter),
- * rcscm_extract(h_out) -- as a CUDA graph owned by the context (replacing any
+/* Capture one full solve step -- rcscm_solve(n_iter, h_out), i.e. setup,
+ * n_iter passes and the Wiener filter -- as a CUDA graph owned by the context (replacing any
  * previous one); rcscm_graph_launch replays it on `stream`.  The graph keeps the
  * context's and h_out's device addresses; the problem buffers must keep them
  * too. */

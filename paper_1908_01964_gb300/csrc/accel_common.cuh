@@ -70,20 +70,34 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
 __device__ __forceinline__ f32x2 rcp2(f32x2 v) { return pk(rcp_approx(lo_of(v)), rcp_approx(hi_of(v))); }
 __device__ __forceinline__ f32x2 dup(float v) { return pk(v, v); }
 
+// Shared memory a RowState needs: per thread and pair, kappa/M and B (read
+// every pass, B also written), kept out of registers so that more rows are
+// resident at once.  Each thread touches only its own entries.
+template <int BLOCK, int NP>
+struct RowSmem {
+    f32x2 kapM[NP][BLOCK];
+    f32x2 B[NP][BLOCK];
+};
+
 // One row with NP pairs of chunks (chunk k = slots k * BLOCK + threadIdx.x;
-// pair q = chunks 2q and 2q + 1), kept in registers.  Slots past the end of
-// the row are padding that contributes exactly zero: r_h = 0 and r_u = 1
-// throughout (their r_h offset beta/(alpha+2) is replaced by 0).
+// pair q = chunks 2q and 2q + 1): invariants tau_ax, sigma_bx and the state in
+// registers, kappa/M and B in the thread's own shared-memory entries.  Slots
+// past the end of the row are padding that contributes exactly zero: r_h = 0
+// and r_u = 1 throughout (their r_h offset beta/(alpha+2) is replaced by 0).
 template <int BLOCK, int NP>
 struct RowState {
-    f32x2 tr[NP], ti[NP], sr[NP], si[NP], kapM[NP], rh[NP], ru[NP], B[NP];
+    f32x2 tr[NP], ti[NP], sr[NP], si[NP], rh[NP], ru[NP];
     f32x2 CB_LAST;
     float lam;
     int J;
+    RowSmem<BLOCK, NP>* sm;
 
-    // invariants tau_ax, sigma_bx, kappa/M (+ r_u floor) of the row starting at slot `off`
-    __device__ __forceinline__ void load_inv(const DevState& d, int64_t off, int J_, const RowConst& c,
-                                             const IterParams& p) {
+    __device__ __forceinline__ explicit RowState(RowSmem<BLOCK, NP>* s) : sm(s) {}
+
+    // Invariants tau_ax, sigma_bx and kappa/M (+ r_u floor) of the row's slots, from
+    // fetch(j, float4& {tau_ax, sigma_bx}, float& kappa) for each slot j < J_.
+    template <class Fetch>
+    __device__ __forceinline__ void load_inv_with(int J_, const RowConst& c, const IterParams& p, Fetch fetch) {
         J = J_;
         const int tid = threadIdx.x;
         float cb_lo = p.c_b, cb_hi = p.c_b;
@@ -94,9 +108,11 @@ struct RowState {
             for (int h = 0; h < 2; ++h) {
                 const int j = (2 * q + h) * BLOCK + tid;
                 if (j < J) {
-                    const float4 t = d.inv4[off + j];
+                    float4 t;
+                    float kap;
+                    fetch(j, t, kap);
                     v[h][0] = t.x; v[h][1] = t.y; v[h][2] = t.z; v[h][3] = t.w;
-                    v[h][4] = fmaf(d.kap[off + j], c.invM, p.ru_floor);   // r_u >= ru_floor by construction
+                    v[h][4] = fmaf(kap, c.invM, p.ru_floor);             // r_u >= ru_floor by construction
                 } else {
                     v[h][0] = v[h][1] = v[h][2] = v[h][3] = 0.f;
                     v[h][4] = 1.f;                                       // padding keeps r_u = 1
@@ -107,10 +123,18 @@ struct RowState {
             ti[q] = pk(v[0][1], v[1][1]);
             sr[q] = pk(v[0][2], v[1][2]);
             si[q] = pk(v[0][3], v[1][3]);
-            kapM[q] = pk(v[0][4], v[1][4]);
-            B[q] = 0;
+            sm->kapM[q][tid] = pk(v[0][4], v[1][4]);
         }
         CB_LAST = pk(cb_lo, cb_hi);
+    }
+
+    // invariants of the row starting at slot `off`, from the context's arrays
+    __device__ __forceinline__ void load_inv(const DevState& d, int64_t off, int J_, const RowConst& c,
+                                             const IterParams& p) {
+        load_inv_with(J_, c, p, [&](int j, float4& t, float& kap) {
+            t = d.inv4[off + j];
+            kap = d.kap[off + j];
+        });
     }
 
     // state from arrays indexed by slot within the row (rh_src[j], ru_src[j]); padding: r_h = 0, r_u = 1
@@ -139,6 +163,10 @@ struct RowState {
             }
         }
     }
+
+    // r_h, r_u of slot k (chunk index) of this thread
+    __device__ __forceinline__ float rh_of(int k) const { return (k & 1) ? hi_of(rh[k >> 1]) : lo_of(rh[k >> 1]); }
+    __device__ __forceinline__ float ru_of(int k) const { return (k & 1) ? hi_of(ru[k >> 1]) : lo_of(ru[k >> 1]); }
 
     __device__ __forceinline__ bool any_clamp(float ru_floor) const {
         bool clamp = false;
@@ -177,14 +205,14 @@ struct RowState {
             part = fma2(Bk, rcp2(ru[q]), part);
             const f32x2 er = fma2(tr[q], NITAA, cr);
             const f32x2 ei = fma2(ti[q], NITAA, ci);
-            ru[q] = fma2(TAAM, fma2(er, er, fma2(ei, ei, Q)), kapM[q]);    // A / M
-            B[q] = Bk;
+            ru[q] = fma2(TAAM, fma2(er, er, fma2(ei, ei, Q)), sm->kapM[q][threadIdx.x]);    // A / M
+            sm->B[q][threadIdx.x] = Bk;
             rh[q] = fma2(rhat, CA2, q == NP - 1 ? CB_LAST : CB);
         }
         lam = block_sum<BLOCK>(lo_of(part) + hi_of(part), red, parity) * invJ;
         const f32x2 ILM = dup(rcp_refined(lam) * c.invM);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) ru[q] = fma2(B[q], ILM, ru[q]);
+        for (int q = 0; q < NP; ++q) ru[q] = fma2(sm->B[q][threadIdx.x], ILM, ru[q]);
     }
 };
 

@@ -58,8 +58,9 @@ __device__ __forceinline__ void block_sum_n(float (&v)[N], float (*red)[BLOCK / 
 
 constexpr int kStage = 2 * kMaxM + 5;                     // x (2M) + g_tau (2) + g_sigma (2) + g_txx
 
-template <int BLOCK>
+template <int BLOCK, int SPT>
 struct AdjShared {
+    RowSmem<BLOCK, SPT / 2> rs;
     float red[2][BLOCK / 32];
     float redn[2][BLOCK / 32][8];
     float2 s_a[kMaxM], s_b[kMaxM], s_Pa[kMaxM], s_P[kMaxM * kMaxM];
@@ -70,9 +71,9 @@ struct AdjShared {
     double dmu[kMaxM];
 };
 
-template <int BLOCK, int NP>
+template <int BLOCK, int NP, int SPT>
 __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs& g, const IterParams& p, int r,
-                                            AdjShared<BLOCK>& sh) {
+                                            AdjShared<BLOCK, SPT>& sh) {
     constexpr int NK = 2 * NP;
     float (*red)[BLOCK / 32] = sh.red;
     float (*redn)[BLOCK / 32][8] = sh.redn;
@@ -116,7 +117,7 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
         s_Pa[tid] = v;
     }
 
-    RowState<BLOCK, NP> st;
+    RowState<BLOCK, NP> st(reinterpret_cast<RowSmem<BLOCK, NP>*>(&sh.rs));
     st.load_inv(d, off, J, c, p);
     float tr[NK], ti[NK], sr[NK], si[NK];
 #pragma unroll
@@ -490,14 +491,14 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
 // forward kernel, so the recomputed states equal the forward ones bit for bit).
 template <int BLOCK, int SPT>
 __global__ void __launch_bounds__(BLOCK) adjoint_kernel(DevState d, AdjointArgs g, IterParams p) {
-    __shared__ AdjShared<BLOCK> sh;
+    __shared__ AdjShared<BLOCK, SPT> sh;
     const int r = blockIdx.x;
     const int np = (d.rows[r].J + 2 * BLOCK - 1) / (2 * BLOCK);
     switch (np) {
-        case 1: adjoint_row<BLOCK, 1>(d, g, p, r, sh); break;
-        case 2: if constexpr (SPT >= 4) adjoint_row<BLOCK, 2>(d, g, p, r, sh); break;
-        case 3: if constexpr (SPT >= 8) adjoint_row<BLOCK, 3>(d, g, p, r, sh); break;
-        case 4: if constexpr (SPT >= 8) adjoint_row<BLOCK, 4>(d, g, p, r, sh); break;
+        case 1: adjoint_row<BLOCK, 1, SPT>(d, g, p, r, sh); break;
+        case 2: if constexpr (SPT >= 4) adjoint_row<BLOCK, 2, SPT>(d, g, p, r, sh); break;
+        case 3: if constexpr (SPT >= 8) adjoint_row<BLOCK, 3, SPT>(d, g, p, r, sh); break;
+        case 4: if constexpr (SPT >= 8) adjoint_row<BLOCK, 4, SPT>(d, g, p, r, sh); break;
         default: break;
     }
 }

@@ -353,6 +353,38 @@ int rcscm_iterate(rcscm_ctx* c, int n_iter, void* stream) {
     return RCSCM_OK;
 }
 
+int rcscm_setup_freq(rcscm_ctx* c, void* stream) {
+    if (!c) return RCSCM_EINVAL;
+    return map_cuda(launch_setup(c->d, (int)c->R, c->opt.null_tol, static_cast<cudaStream_t>(stream)));
+}
+
+static bool fused_config(const rcscm_options& o) {
+    return o.rule == RCSCM_RULE_ACCEL && o.iters_per_launch == 0 && o.ckpt_stride == 0;
+}
+
+int rcscm_run(rcscm_ctx* c, int n_iter, void* h_out, void* stream) {
+    if (!c || n_iter < 0 || !h_out || !fused_config(c->opt)) return RCSCM_EINVAL;
+    const cudaError_t e = launch_accel(c->d, (int)c->R, c->max_j, c->opt.block, n_iter, iter_params(c->opt),
+                                       c->opt.persistent != 0, static_cast<cudaStream_t>(stream),
+                                       static_cast<float2*>(h_out));
+    c->iters_done = n_iter;
+    c->iter_block = c->opt.block;
+    return map_cuda(e);
+}
+
+int rcscm_solve(rcscm_ctx* c, int n_iter, void* h_out, void* stream) {
+    if (!c || n_iter < 0 || !h_out) return RCSCM_EINVAL;
+    if (!fused_config(c->opt)) {             // the same work as separate calls
+        int st = rcscm_setup(c, stream);
+        if (!st) st = rcscm_iterate(c, n_iter, stream);
+        if (!st) st = rcscm_extract(c, h_out, stream);
+        return st;
+    }
+    int st = rcscm_setup_freq(c, stream);
+    if (!st) st = rcscm_run(c, n_iter, h_out, stream);
+    return st;
+}
+
 int rcscm_extract(rcscm_ctx* c, void* h_out, void* stream) {
     if (!c || !h_out) return RCSCM_EINVAL;
     return map_cuda(launch_extract(c->d, c->n_blocks, static_cast<float2*>(h_out),
@@ -546,9 +578,7 @@ int rcscm_graph_create(rcscm_ctx* c, int n_iter, void* h_out) {
     if (e != cudaSuccess) return map_cuda(e);
     e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return map_cuda(e);
-    int st = rcscm_setup(c, c->cap_stream);
-    if (!st) st = rcscm_iterate(c, n_iter, c->cap_stream);
-    if (!st) st = rcscm_extract(c, h_out, c->cap_stream);
+    int st = rcscm_solve(c, n_iter, h_out, c->cap_stream);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
     if (st) {
@@ -616,9 +646,7 @@ int rcscm_solve_host(int64_t I, int64_t J, int64_t M, const void* x, const void*
         q.x = dx; q.a = da; q.Rp = dR; q.lambda0 = dl; q.rh0 = drh; q.ru0 = dru;
         st = rcscm_create(&c, &q, 1, opt, nullptr);
     }
-    if (!st) st = rcscm_setup(c, nullptr);
-    if (!st) st = rcscm_iterate(c, n_iter, nullptr);
-    if (!st) st = rcscm_extract(c, dh, nullptr);
+    if (!st) st = rcscm_solve(c, n_iter, dh, nullptr);
     if (!st) st = map_cuda(cudaMemcpy(h_out, dh, nx * sizeof(float2), cudaMemcpyDeviceToHost));
     if (!st && (rh || ru || lambda)) {
         // reuse the input state buffers as staging for the outputs

@@ -29,11 +29,8 @@ __global__ void __launch_bounds__(kSlotBlock) extract_kernel(DevState d, float2*
         const int64_t s = rd->slot_off + bm.j0 + t;
         const float4 tv = d.inv4[s];
         const float rh = d.rh[s], ru = d.ru[s];
-        const float2 sab = make_float2(c.sab_re, c.sab_im);
-        const float2 rax = cadd(make_float2(tv.x, tv.y), cscale(cmul(sab, make_float2(tv.z, tv.w)), 1.0f / lam));
-        const float raa = c.taa + c.sab2 / lam;
-        const float2 w = cscale(rax, rh / (ru + rh * raa));
-        for (int m = 0; m < M; ++m) sh[t * M + m] = cmul(w, sa[m]);
+        const float2 w = wiener_weight(c.taa, c.sab2, make_float2(c.sab_re, c.sab_im), lam, tv, rh, ru);
+        for (int m = 0; m < M; ++m) sh[t * M + m] = cmul_exact(w, sa[m]);
     }
     __syncthreads();
     // write the block's n * M outputs (contiguous) with coalesced 16-byte stores when aligned

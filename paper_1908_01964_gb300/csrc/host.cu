@@ -141,9 +141,7 @@ extern "C" int rcscm_host_run(rcscm_host* p, const void* x, const void* a, const
         if (e == cudaSuccess) e = cudaMemcpyAsync(p->ru0 + r0 * J, ru0 + r0 * J, bs, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) break;
         rcscm_ctx* ctx = p->ctx[(size_t)c];
-        st = rcscm_setup(ctx, s);
-        if (!st) st = rcscm_iterate(ctx, n_iter, s);
-        if (!st) st = rcscm_extract(ctx, p->h + r0 * J * M, s);
+        st = rcscm_solve(ctx, n_iter, p->h + r0 * J * M, s);
         if (!st && (rh || ru || lambda))
             st = rcscm_get_state(ctx, 0, p->rh + r0 * J, p->ru + r0 * J, p->lam + r0, s);
         if (st) break;

@@ -132,6 +132,76 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
+// Per-slot invariants from the row's projection Phi (M x M, row-major, Phi x:
+// row 0 gives tau_ax, row M-1 sigma_bx, rows 1..M-2 the components whose squared
+// norm is kappa = tau_xx - |tau_ax|^2 / tau_aa).  out = {tau_ax, sigma_bx}.
+template <int M>
+__device__ __forceinline__ void project_slot(const float2* __restrict__ phi, const float2* __restrict__ xs,
+                                             float4& out, float& kappa) {
+    float2 xv[M];
+#pragma unroll
+    for (int n = 0; n < M; ++n) xv[n] = xs[n];
+    float2 z0 = make_float2(0.f, 0.f), zb = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int n = 0; n < M; ++n) {
+        z0 = cfma(phi[n], xv[n], z0);
+        zb = cfma(phi[(M - 1) * M + n], xv[n], zb);
+    }
+    float kap = 0.f;
+#pragma unroll
+    for (int k = 1; k <= M - 2; ++k) {
+        float2 zk = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int n = 0; n < M; ++n) zk = cfma(phi[k * M + n], xv[n], zk);
+        kap += cabs2(zk);
+    }
+    out = make_float4(z0.x, z0.y, zb.x, zb.y);
+    kappa = kap;
+}
+
+// Projection of one slot for a runtime M (2..8).
+__device__ __forceinline__ void project_slot_m(int M, const float2* __restrict__ phi, const float2* __restrict__ xs,
+                                               float4& out, float& kappa) {
+    switch (M) {
+        case 2: project_slot<2>(phi, xs, out, kappa); break;
+        case 3: project_slot<3>(phi, xs, out, kappa); break;
+        case 4: project_slot<4>(phi, xs, out, kappa); break;
+        case 5: project_slot<5>(phi, xs, out, kappa); break;
+        case 6: project_slot<6>(phi, xs, out, kappa); break;
+        case 7: project_slot<7>(phi, xs, out, kappa); break;
+        default: project_slot<8>(phi, xs, out, kappa); break;
+    }
+}
+
+// Wiener weight w of the posterior mean h = w a (Sec. II-A; Sherman-Morrison,
+// Eq. (eq:rijxinv)): w = r_h rho_ax / (r_u + r_h rho_aa) with rho_ax = tau_ax +
+// sigma_ab sigma_bx / lambda and rho_aa = tau_aa + |sigma_ab|^2 / lambda.
+// Every operation is explicit (fmaf, IEEE division), so each kernel that calls it
+// rounds identically.
+__device__ __forceinline__ float2 wiener_weight(float taa, float sab2, float2 sab, float lam, float4 inv, float rh,
+                                                float ru) {
+    const float il = 1.0f / lam;
+    const float ur = fmaf(sab.x, inv.z, -(sab.y * inv.w));      // sigma_ab sigma_bx
+    const float ui = fmaf(sab.x, inv.w, sab.y * inv.z);
+    const float raxr = fmaf(ur, il, inv.x), raxi = fmaf(ui, il, inv.y);
+    const float raa = fmaf(sab2, il, taa);
+    const float k = rh / fmaf(rh, raa, ru);
+    return make_float2(raxr * k, raxi * k);
+}
+
+// w a_m with explicit fused multiply-adds (identical rounding in every kernel).
+__device__ __forceinline__ float2 cmul_exact(float2 w, float2 a) {
+    return make_float2(fmaf(w.x, a.x, -(w.y * a.y)), fmaf(w.x, a.y, w.y * a.x));
+}
+
+// Minimum resident CTAs per SM requested from the compiler for the accelerated
+// kernels: with kappa/M and B in shared memory, 128 x 8 fits 7 CTAs (72
+// registers) and 256 x 8 fits 3 (80), so rows of up to 1024 / 2048 frames keep
+// more rows resident at once; other shapes are left to the compiler.
+constexpr int accel_min_blocks(int block, int spt) {
+    return (block == 128 && spt == 8) ? 7 : ((block == 256 && spt == 8) ? 3 : 0);
+}
+
 // Butterfly sum over a warp: every lane ends with the same, order-fixed value.
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -180,8 +250,10 @@ namespace rcscm {
 int* ctx_status_word(rcscm_ctx* c);
 cudaError_t launch_setup(const DevState& d, int n_rows, double null_tol, cudaStream_t s);
 cudaError_t launch_invariants(const DevState& d, int n_blocks, cudaStream_t s);
+// h != nullptr: the fused form (invariants from x, the passes, then the Wiener
+// output into h), for a state freshly set by the setup kernel.
 cudaError_t launch_accel(const DevState& d, int n_rows, int max_j, int block, int n_iter,
-                         const IterParams& p, bool persistent, cudaStream_t s);
+                         const IterParams& p, bool persistent, cudaStream_t s, float2* h = nullptr);
 // Observed-data log posterior: per slot block partials, then per-utterance sums
 // (block ranges [first_block[p], first_block[p + 1])) into out[p].
 cudaError_t launch_objective(const DevState& d, int n_blocks, const IterParams& p, double alpha, double beta,

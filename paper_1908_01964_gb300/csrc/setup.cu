@@ -379,29 +379,6 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     }
 }
 
-template <int M>
-__device__ __forceinline__ void project_slot(const float2* __restrict__ phi, const float2* __restrict__ xs,
-                                             float4& out, float& kappa) {
-    float2 xv[M];
-#pragma unroll
-    for (int n = 0; n < M; ++n) xv[n] = xs[n];
-    float2 z0 = make_float2(0.f, 0.f), zb = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int n = 0; n < M; ++n) {
-        z0 = cfma(phi[n], xv[n], z0);
-        zb = cfma(phi[(M - 1) * M + n], xv[n], zb);
-    }
-    float kap = 0.f;
-#pragma unroll
-    for (int k = 1; k <= M - 2; ++k) {
-        float2 zk = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int n = 0; n < M; ++n) zk = cfma(phi[k * M + n], xv[n], zk);
-        kap += cabs2(zk);
-    }
-    out = make_float4(z0.x, z0.y, zb.x, zb.y);
-    kappa = kap;
-}
 
 __global__ void __launch_bounds__(kSlotBlock) invariants_kernel(DevState d) {
     __shared__ float2 sphi[kMaxM * kMaxM];
@@ -430,15 +407,7 @@ __global__ void __launch_bounds__(kSlotBlock) invariants_kernel(DevState d) {
     const float2* xs = sx + t * M;
     float4 o;
     float kap;
-    switch (M) {
-        case 2: project_slot<2>(sphi, xs, o, kap); break;
-        case 3: project_slot<3>(sphi, xs, o, kap); break;
-        case 4: project_slot<4>(sphi, xs, o, kap); break;
-        case 5: project_slot<5>(sphi, xs, o, kap); break;
-        case 6: project_slot<6>(sphi, xs, o, kap); break;
-        case 7: project_slot<7>(sphi, xs, o, kap); break;
-        default: project_slot<8>(sphi, xs, o, kap); break;
-    }
+    project_slot_m(M, sphi, xs, o, kap);
     const int64_t s = rd->slot_off + j;
     d.inv4[s] = o;
     d.kap[s] = kap;

@@ -88,6 +88,9 @@ def lib():
         "rcscm_graph_create": (c_int, [vp, c_int, vp]),
         "rcscm_graph_launch": (c_int, [vp, vp]),
         "rcscm_backward": (c_int, [vp, vp, vp, vp, vp, vp]),
+        "rcscm_setup_freq": (c_int, [vp, vp]),
+        "rcscm_run": (c_int, [vp, c_int, vp, vp]),
+        "rcscm_solve": (c_int, [vp, c_int, vp, vp]),
         "rcscm_host_create": (c_int, [POINTER(vp), c_int64, c_int64, c_int64, POINTER(Options), c_int]),
         "rcscm_host_run": (c_int, [vp, vp, vp, vp, vp, vp, vp, c_int, vp, vp, vp, vp]),
         "rcscm_host_destroy": (None, [vp]),
@@ -213,6 +216,30 @@ class Solver:
         elif out.dtype != torch.complex64 or out.numel() != self.out_elements or not out.is_contiguous():
             raise ValueError("out must be a contiguous complex64 tensor with one element per output")
         _check(lib().rcscm_extract(self.ctx, c_void_p(out.data_ptr()), _stream(stream)), "rcscm_extract")
+        return out
+
+    def _out(self, out):
+        import torch
+        if out is None:
+            return torch.empty(self.out_elements, dtype=torch.complex64, device=self.device)
+        if out.dtype != torch.complex64 or out.numel() != self.out_elements or not out.is_contiguous():
+            raise ValueError("out must be a contiguous complex64 tensor with one element per output")
+        return out
+
+    def setup_freq(self, stream=None):
+        """Per-frequency setup only (rcscm_setup_freq)."""
+        _check(lib().rcscm_setup_freq(self.ctx, _stream(stream)), "rcscm_setup_freq")
+
+    def run(self, n_iter: int, out=None, stream=None):
+        """Invariants + n_iter passes + Wiener output from the initial state, one launch."""
+        out = self._out(out)
+        _check(lib().rcscm_run(self.ctx, int(n_iter), c_void_p(out.data_ptr()), _stream(stream)), "rcscm_run")
+        return out
+
+    def solve(self, n_iter: int, out=None, stream=None):
+        """setup + n_iter passes + Wiener output (rcscm_solve)."""
+        out = self._out(out)
+        _check(lib().rcscm_solve(self.ctx, int(n_iter), c_void_p(out.data_ptr()), _stream(stream)), "rcscm_solve")
         return out
 
     def split(self, flat):

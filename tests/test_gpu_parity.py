@@ -359,3 +359,37 @@ def test_single_m4_full_size_sampled_rows():
     assert max(e["rh"], e["ru"], e["lam"]) < TOL_FULL_RUN, e
     assert e["sdr"] > SDR_MIN_DB, e
     assert np.all(np.isfinite(g["h"])) and np.all(g["ru"] > 0) and np.all(g["rh"] > 0)
+
+
+def test_scale_m8_precision_at_1_10_200_passes():
+    """Precision at scale: M = 8 circular array, I = 2049, J = 4000 (8.2 M slots),
+    200 passes.  Relative errors of r_h, r_u, lambda after passes 1, 10 and 200
+    and of the extracted target, on sampled rows against the FP64 oracle."""
+    import torch
+    from paper_1908_01964_gb300 import rcscm as R
+    wl = synth.workload("scale-m8")
+    p = synth.make_workload(wl)[0]
+    I = p["x"].shape[0]
+    rows = sorted(set([0, 1, 2, I // 2, I - 2, I - 1] + list(np.random.default_rng(1).choice(I, 6, replace=False))))
+    hist = []
+    o = O.run(p, wl.n_iter, "accel2", alpha=ALPHA, beta=BETA, rows=rows, history=hist)
+    d = R.to_device(p)
+    errs = {}
+    with R.Solver([d]) as s:
+        s.setup()
+        done = 0
+        for k in (1, 10, 200):
+            s.iterate(k - done)
+            done = k
+            rh, ru, lam = (t.cpu().numpy()[rows] for t in s.get_state(0))
+            orh, oru, olam = hist[k - 1]
+            errs[k] = dict(rh=rel(rh, orh), ru=rel(ru, oru), lam=rel(lam, olam))
+        h = s.extract().view(p["x"].shape).cpu().numpy()[rows]
+        st = s.status()
+        torch.cuda.synchronize()
+    errs["sdr_200"] = sdr_db(h, o["h"])
+    report("scale_m8_precision", rows=len(rows), errors=errs, status=st)
+    assert st == 0
+    assert max(errs[1].values()) < TOL_ONE_ITER, errs
+    assert max(errs[10].values()) < TOL_FULL_RUN and max(errs[200].values()) < TOL_FULL_RUN, errs
+    assert errs["sdr_200"] > SDR_MIN_DB, errs
