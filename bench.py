@@ -71,7 +71,9 @@ def parse():
     ap.add_argument("--replicas", type=int, default=1,
                     help="solve R copies of the workload in one context (inputs shared, state per copy)")
     ap.add_argument("--no-streaming", action="store_true", help="skip the streaming-mode HBM roofline section")
-    ap.add_argument("--streaming-replicas", type=int, default=8)
+    ap.add_argument("--streaming-workload", default="scale-m8",
+                    help="workload of the streaming section (its invariants + state must exceed L2)")
+    ap.add_argument("--streaming-replicas", type=int, default=1)
     ap.add_argument("--streaming-launches", type=int, default=50)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward + adjoint section")
     ap.add_argument("--adjoint-workload", default="adjoint-16")
@@ -155,8 +157,10 @@ def load_peaks():
 # Kernel sources whose hash a profile summary records: a traffic figure is used
 # only while the kernel it was measured on is unchanged.
 KERNEL_SOURCES = {
-    "accel_kernel": ["accel_common.cuh", "iterate.cu", "rcscm_internal.cuh"],
-    "solve_kernel": ["accel_common.cuh", "iterate.cu", "rcscm_internal.cuh"],
+    "accel_kernel": ["accel_common.cuh", "iterate_impl.cuh", "rcscm_internal.cuh"],
+    "solve_kernel": ["accel_common.cuh", "iterate_impl.cuh", "rcscm_internal.cuh"],
+    "setup_kernel": ["setup.cu", "rcscm_internal.cuh"],
+    "naive_kernel": ["naive.cu", "rcscm_internal.cuh"],
     "adjoint_kernel": ["accel_common.cuh", "adjoint.cu", "rcscm_internal.cuh"],
 }
 
@@ -486,7 +490,8 @@ def run_ours(args):
 
     # ---------------- streaming mode: one pass per launch over a working set larger than L2
     if not args.no_streaming and args.rule == "accel":
-        result["streaming"] = streaming_roofline(dprobs[:len(probs)], args, R, peaks, stream)
+        same = args.streaming_workload == args.workload and args.replicas == 1
+        result["streaming"] = streaming_roofline(args, R, dev, peaks, stream, reuse=(wl, dprobs) if same else None)
 
     # ---------------- adjoint (forward with checkpoints + rcscm_backward)
     if not args.no_adjoint and args.rule == "accel":
@@ -506,11 +511,16 @@ def run_ours(args):
     return result if rank == 0 else None
 
 
-def streaming_roofline(dprobs, args, R, peaks, stream):
+def streaming_roofline(args, R, dev, peaks, stream, reuse=None):
     """HBM roofline of the accelerated kernel run one pass per launch (state
-    streamed through HBM each pass) on copies of the workload whose invariants
-    + state exceed L2: 36 algorithmic bytes per slot per launch."""
+    streamed through HBM each pass) on a workload whose invariants + state
+    exceed L2: 36 algorithmic bytes per slot per launch."""
     import torch
+    if reuse is not None:
+        wl, dprobs = reuse
+    else:
+        wl, probs = make_inputs(args.streaming_workload)
+        dprobs = [R.to_device(p, dev) for p in probs]
     copies = dprobs * args.streaming_replicas
     s = R.Solver(copies, rule="accel", iters_per_launch=1, block=args.block)
     slots = s.info()["slots"]
@@ -532,13 +542,13 @@ def streaming_roofline(dprobs, args, R, peaks, stream):
     bytes_ = ACCEL_BYTES_PER_SLOT_LAUNCH * slots
     achieved = bytes_ / (t / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    traffic, tsrc = profiled_traffic("accel_kernel", f"{args.workload}-x{args.streaming_replicas}-streaming")
+    traffic, tsrc = profiled_traffic("accel_kernel", f"{wl.name}-x{args.streaming_replicas}-streaming")
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_source": tsrc, "traffic_algorithmic": bytes_,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured burst copy)" if peaks else "fallback 6800 GB/s",
             "kernel": "accel_kernel, 1 pass per launch",
-            "workload": f"{args.streaming_replicas} copies of the bench workload in one context, {slots} slots, "
-                        f"{bytes_ / 1e6:.0f} MB per launch (invariants + state > L2)",
+            "workload": f"{wl.name}" + (f" x{args.streaming_replicas}" if args.streaming_replicas > 1 else "")
+                        + f", {slots} slots, {bytes_ / 1e6:.0f} MB per launch (invariants + state > L2)",
             "launch_us_median": 1e3 * t, "launches": n, "slot_updates_per_s": slots / (t / 1e3),
             "status": R.strerror(code)}
 

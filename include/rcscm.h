@@ -85,8 +85,8 @@ typedef struct {
     double null_tol;         /* zero-eigenvalue test: mu_1 <= null_tol * mu_M (1e-6)   */
     int    block;            /* threads per row of the accelerated kernel: 0 = choose
                                 by J, else 32, 64, 128, 256, 512 or 1024; rows may be
-                                up to 16*block (block <= 128), 8*block (256, 512) or
-                                4096 (1024) frames long                                */
+                                up to 8*block (block <= 512) or 4096 (1024) frames
+                                long                                                   */
     int    iters_per_launch; /* 0: every iteration of one rcscm_iterate call in one
                                 register-resident launch; k > 0: one launch per k
                                 iterations, state streamed through HBM between them    */

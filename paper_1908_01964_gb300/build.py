@@ -20,6 +20,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librcscm.so")
 SOURCES = ["api.cu", "setup.cu", "iterate.cu", "naive.cu", "extract.cu", "objective.cu", "host.cu", "noalloc.cu", "adjoint.cu"]
+# (threads per row, slots per thread) shapes of the accelerated kernels: iterate_inst.cu
+# is compiled once per shape so that the large unrolled kernels build in parallel.
+INSTANCES = [(32, 4), (32, 8), (64, 4), (64, 8), (128, 4), (128, 8), (256, 4), (256, 8), (512, 4), (512, 8),
+             (1024, 4)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -32,7 +36,7 @@ def nvcc_path() -> str:
 
 
 def _inputs():
-    files = [os.path.join(CSRC, s) for s in SOURCES]
+    files = [os.path.join(CSRC, s) for s in SOURCES + ["iterate_inst.cu"]]
     files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     files.append(os.path.join(INCLUDE, "rcscm.h"))
     return files
@@ -54,9 +58,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     flags = NVCC_FLAGS + list(extra_flags or [])
     procs = []
     objs = []
-    for src in SOURCES:
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *flags, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
+    units = [(src, src.replace(".cu", ".o"), []) for src in SOURCES]
+    units += [("iterate_inst.cu", f"iterate_b{b}_s{t}.o", [f"-DRCSCM_INST_BLOCK={b}", f"-DRCSCM_INST_SPT={t}"])
+              for b, t in INSTANCES]
+    for src, objname, defs in units:
+        obj = os.path.join(BUILD_DIR, objname)
+        cmd = [nvcc, *ARCH, *flags, *defs, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

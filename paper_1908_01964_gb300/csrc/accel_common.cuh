@@ -50,11 +50,13 @@ __device__ __forceinline__ f32x2 pk(float lo, float hi) {
 __device__ __forceinline__ float lo_of(f32x2 v) {
     float a, b;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    (void)b;
     return a;
 }
 __device__ __forceinline__ float hi_of(f32x2 v) {
     float a, b;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    (void)a;
     return b;
 }
 __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
@@ -70,29 +72,65 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
 __device__ __forceinline__ f32x2 rcp2(f32x2 v) { return pk(rcp_approx(lo_of(v)), rcp_approx(hi_of(v))); }
 __device__ __forceinline__ f32x2 dup(float v) { return pk(v, v); }
 
-// Shared memory a RowState needs: per thread and pair, kappa/M and B (read
-// every pass, B also written), kept out of registers so that more rows are
-// resident at once.  Each thread touches only its own entries.
-template <int BLOCK, int NP>
-struct RowSmem {
-    f32x2 kapM[NP][BLOCK];
-    f32x2 B[NP][BLOCK];
+// Per-pass row scalars of Algorithm 2, duplicated into both halves of a pair.
+struct PassConsts {
+    f32x2 NSR, NSI, SI, SAB2, NITAA, TAAM, CA2, CB, RTAA, SLR, SLI, NSLI;
 };
+__device__ __forceinline__ PassConsts pass_consts(const RowConst& c, const IterParams& p, float lam) {
+    PassConsts k;
+    k.NSR = dup(-c.sab_re);
+    k.NSI = dup(-c.sab_im);
+    k.SI = dup(c.sab_im);
+    k.SAB2 = dup(c.sab2);
+    k.NITAA = dup(-c.inv_taa);
+    k.TAAM = dup(c.taaM);
+    k.CA2 = dup(p.c_a2);
+    k.CB = dup(p.c_b);
+    const float il = rcp_refined(lam);
+    k.RTAA = dup(fmaf(c.sab2, il, c.taa));                       // rho~_aa, Eq. (eq:traa_accel)
+    const float slr = c.sab_re * il, sli = c.sab_im * il;
+    k.SLR = dup(slr);
+    k.SLI = dup(sli);
+    k.NSLI = dup(-sli);
+    return k;
+}
+
+// Pass A of one pair of slots (Algorithm 2 before the lambda update): r_h is
+// replaced by its new value, r_u by A/M (the part of the new r_u that needs no
+// lambda), B is returned, and B / r~_u is added to the lambda partial sum.
+// `cb` is the r_h offset beta/(alpha+2), 0 in padding slots.
+__device__ __forceinline__ void pass_a_pair(const PassConsts& k, f32x2 tr, f32x2 ti, f32x2 sr, f32x2 si, f32x2 kapM,
+                                            f32x2 cb, f32x2& rh, f32x2& ru, f32x2& Bout, f32x2& part) {
+    const f32x2 pr = fma2(k.SLR, sr, fma2(k.NSLI, si, tr));
+    const f32x2 pi = fma2(k.SLR, si, fma2(k.SLI, sr, ti));
+    const f32x2 g = mul2(rh, rcp2(fma2(rh, k.RTAA, ru)));
+    const f32x2 cr = mul2(g, pr), ci = mul2(g, pi);
+    const f32x2 Q = mul2(g, ru);
+    const f32x2 rhat = fma2(ci, ci, fma2(cr, cr, Q));
+    const f32x2 dr = fma2(cr, k.NSR, fma2(ci, k.NSI, sr));
+    const f32x2 di = fma2(ci, k.NSR, fma2(cr, k.SI, si));
+    const f32x2 Bk = fma2(dr, dr, fma2(di, di, mul2(Q, k.SAB2)));
+    part = fma2(Bk, rcp2(ru), part);
+    const f32x2 er = fma2(tr, k.NITAA, cr);
+    const f32x2 ei = fma2(ti, k.NITAA, ci);
+    ru = fma2(k.TAAM, fma2(er, er, fma2(ei, ei, Q)), kapM);              // A / M
+    Bout = Bk;
+    rh = fma2(rhat, k.CA2, cb);
+}
 
 // One row with NP pairs of chunks (chunk k = slots k * BLOCK + threadIdx.x;
-// pair q = chunks 2q and 2q + 1): invariants tau_ax, sigma_bx and the state in
-// registers, kappa/M and B in the thread's own shared-memory entries.  Slots
-// past the end of the row are padding that contributes exactly zero: r_h = 0
-// and r_u = 1 throughout (their r_h offset beta/(alpha+2) is replaced by 0).
+// pair q = chunks 2q and 2q + 1), kept in registers.  Slots past the end of
+// the row are padding that contributes exactly zero: r_h = 0 and r_u = 1
+// throughout (their r_h offset beta/(alpha+2) is replaced by 0).  (Keeping
+// kappa/M and B in shared memory instead, with launch bounds for more resident
+// rows, measured slower: the extra loads and spills cost more than the wave
+// tail they remove.)
 template <int BLOCK, int NP>
 struct RowState {
-    f32x2 tr[NP], ti[NP], sr[NP], si[NP], rh[NP], ru[NP];
+    f32x2 tr[NP], ti[NP], sr[NP], si[NP], kapM[NP], rh[NP], ru[NP], B[NP];
     f32x2 CB_LAST;
     float lam;
     int J;
-    RowSmem<BLOCK, NP>* sm;
-
-    __device__ __forceinline__ explicit RowState(RowSmem<BLOCK, NP>* s) : sm(s) {}
 
     // Invariants tau_ax, sigma_bx and kappa/M (+ r_u floor) of the row's slots, from
     // fetch(j, float4& {tau_ax, sigma_bx}, float& kappa) for each slot j < J_.
@@ -123,7 +161,8 @@ struct RowState {
             ti[q] = pk(v[0][1], v[1][1]);
             sr[q] = pk(v[0][2], v[1][2]);
             si[q] = pk(v[0][3], v[1][3]);
-            sm->kapM[q][tid] = pk(v[0][4], v[1][4]);
+            kapM[q] = pk(v[0][4], v[1][4]);
+            B[q] = 0;
         }
         CB_LAST = pk(cb_lo, cb_hi);
     }
@@ -183,36 +222,16 @@ struct RowState {
     // fixed-order block reduction, pass B per slot.  `parity` selects the half of `red`.
     __device__ __forceinline__ void pass(const RowConst& c, const IterParams& p,
                                          float (*red)[BLOCK / 32 > 0 ? BLOCK / 32 : 1], int parity) {
-        const f32x2 NSR = dup(-c.sab_re), NSI = dup(-c.sab_im), SI = dup(c.sab_im), SAB2 = dup(c.sab2);
-        const f32x2 NITAA = dup(-c.inv_taa), TAAM = dup(c.taaM), CA2 = dup(p.c_a2), CB = dup(p.c_b);
-        const float invJ = 1.0f / (float)J;
-        const float il = rcp_refined(lam);
-        const f32x2 RTAA = dup(fmaf(c.sab2, il, c.taa));          // rho~_aa, Eq. (eq:traa_accel)
-        const float slr = c.sab_re * il, sli = c.sab_im * il;
-        const f32x2 SLR = dup(slr), SLI = dup(sli), NSLI = dup(-sli);
+        const PassConsts k = pass_consts(c, p, lam);
         f32x2 part = dup(0.f);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            const f32x2 pr = fma2(SLR, sr[q], fma2(NSLI, si[q], tr[q]));
-            const f32x2 pi = fma2(SLR, si[q], fma2(SLI, sr[q], ti[q]));
-            const f32x2 g = mul2(rh[q], rcp2(fma2(rh[q], RTAA, ru[q])));
-            const f32x2 cr = mul2(g, pr), ci = mul2(g, pi);
-            const f32x2 Q = mul2(g, ru[q]);
-            const f32x2 rhat = fma2(ci, ci, fma2(cr, cr, Q));
-            const f32x2 dr = fma2(cr, NSR, fma2(ci, NSI, sr[q]));
-            const f32x2 di = fma2(ci, NSR, fma2(cr, SI, si[q]));
-            const f32x2 Bk = fma2(dr, dr, fma2(di, di, mul2(Q, SAB2)));
-            part = fma2(Bk, rcp2(ru[q]), part);
-            const f32x2 er = fma2(tr[q], NITAA, cr);
-            const f32x2 ei = fma2(ti[q], NITAA, ci);
-            ru[q] = fma2(TAAM, fma2(er, er, fma2(ei, ei, Q)), sm->kapM[q][threadIdx.x]);    // A / M
-            sm->B[q][threadIdx.x] = Bk;
-            rh[q] = fma2(rhat, CA2, q == NP - 1 ? CB_LAST : CB);
-        }
-        lam = block_sum<BLOCK>(lo_of(part) + hi_of(part), red, parity) * invJ;
+        for (int q = 0; q < NP; ++q)
+            pass_a_pair(k, tr[q], ti[q], sr[q], si[q], kapM[q], q == NP - 1 ? CB_LAST : k.CB, rh[q], ru[q], B[q],
+                        part);
+        lam = block_sum<BLOCK>(lo_of(part) + hi_of(part), red, parity) * (1.0f / (float)J);
         const f32x2 ILM = dup(rcp_refined(lam) * c.invM);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) ru[q] = fma2(sm->B[q][threadIdx.x], ILM, ru[q]);
+        for (int q = 0; q < NP; ++q) ru[q] = fma2(B[q], ILM, ru[q]);
     }
 };
 

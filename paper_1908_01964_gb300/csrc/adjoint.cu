@@ -10,9 +10,10 @@
 // adjoint_kernel<BLOCK, NP>: one CTA per row, NP pairs of chunks per thread
 // (the forward kernel's RowState).  Steps:
 //   1. Wiener filter h = w a, w = r_h rho_ax / (r_u + r_h rho_aa), at the final state.
-//   2. Passes t = K-1 .. 0: the state entering pass t is recomputed from the
-//      nearest checkpoint with the forward pass code, then the pass is run
-//      backwards (two fixed-order block reductions per pass).
+//   2. Passes t = K-1 .. 0 by checkpoint segments: each segment is recomputed
+//      once from its checkpoint with the forward pass code (bit-exact states,
+//      kept in a scratch), then its passes are run backwards (two fixed-order
+//      block reductions per pass).
 //   3. Invariants: kappa = tau_xx - |tau_ax|^2 / tau_aa, tau_ax = a^H P x,
 //      tau_xx = x^H P x, sigma_bx = b^H x with P = (R')^+ (Eq. (eq:riinv)):
 //      g_x = P a g_tau + 2 g_txx P x + b g_sigma per slot, and the row sums
@@ -60,7 +61,6 @@ constexpr int kStage = 2 * kMaxM + 5;                     // x (2M) + g_tau (2) 
 
 template <int BLOCK, int SPT>
 struct AdjShared {
-    RowSmem<BLOCK, SPT / 2> rs;
     float red[2][BLOCK / 32];
     float redn[2][BLOCK / 32][8];
     float2 s_a[kMaxM], s_b[kMaxM], s_Pa[kMaxM], s_P[kMaxM * kMaxM];
@@ -117,7 +117,7 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
         s_Pa[tid] = v;
     }
 
-    RowState<BLOCK, NP> st(reinterpret_cast<RowSmem<BLOCK, NP>*>(&sh.rs));
+    RowState<BLOCK, NP> st;
     st.load_inv(d, off, J, c, p);
     float tr[NK], ti[NK], sr[NK], si[NK];
 #pragma unroll
@@ -216,117 +216,131 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
         g_lam = -gil * il * il;                                     // adjoint of lambda after the last pass
     }
 
-    // ---- 2. passes t = K-1 .. 0 ------------------------------------------------------------
+    // ---- 2. passes t = K-1 .. 0, one checkpoint segment at a time ----------------------------
+    // Each segment is recomputed once from its checkpoint with the forward pass code; the
+    // state entering each of its passes goes to the segment scratch (each thread its own
+    // slots, lambda by thread 0, read after the passes' barriers), then the passes are
+    // reversed from the scratch.
     int parity = 1;                                                 // the next reduction uses half 1
-    for (int t = g.K - 1; t >= 0; --t) {
-        const int ck = t / g.stride;
-        const float* crh = g.ckpt_rh + (size_t)ck * g.S + off;
-        const float* cru = g.ckpt_ru + (size_t)ck * g.S + off;
-        st.load_state(crh, cru, g.ckpt_lam[(size_t)ck * g.R + r]);
-        for (int u = ck * g.stride; u < t; ++u) st.pass(c, p, red, (parity++) & 1);
-        // state entering pass t
-        float rh_t[NK], ru_t[NK];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            rh_t[2 * q] = lo_of(st.rh[q]); rh_t[2 * q + 1] = hi_of(st.rh[q]);
-            ru_t[2 * q] = lo_of(st.ru[q]); ru_t[2 * q + 1] = hi_of(st.ru[q]);
+    const int n_seg = (g.K + g.stride - 1) / g.stride;
+    for (int seg = n_seg - 1; seg >= 0; --seg) {
+        const int t0 = seg * g.stride, t1 = min(g.K, t0 + g.stride);
+        st.load_state(g.ckpt_rh + (size_t)seg * g.S + off, g.ckpt_ru + (size_t)seg * g.S + off,
+                      g.ckpt_lam[(size_t)seg * g.R + r]);
+        for (int t = t0; t < t1; ++t) {
+            st.store_state(g.seg_rh + (size_t)(t - t0) * g.S + off, g.seg_ru + (size_t)(t - t0) * g.S + off);
+            if (tid == 0) g.seg_lam[(size_t)(t - t0) * g.R + r] = st.lam;
+            st.pass(c, p, red, (parity++) & 1);
         }
-        const float lam_t = st.lam;
-        st.pass(c, p, red, (parity++) & 1);                      // lambda after pass t (same code as forward)
-        const float lam1 = st.lam;
-        const float il = rcp_refined(lam_t);
-        const float rtaa = fmaf(c.sab2, il, c.taa);
-        const float slr = c.sab_re * il, sli = c.sab_im * il;
-        const float ilM = rcp_refined(lam1) * c.invM;
-        // S1 = sum_j g_ru'_j B_j  (B needs the forward intermediates)
-        float Bk[NK], rru[NK];
-        float s1 = 0.f;
+        const float lam_end = st.lam;                               // lambda after pass t1 - 1
+        for (int t = t1 - 1; t >= t0; --t) {
+            // state entering pass t, and lambda after it
+            float rh_t[NK], ru_t[NK];
+            {
+                const float* srh = g.seg_rh + (size_t)(t - t0) * g.S + off;
+                const float* sru = g.seg_ru + (size_t)(t - t0) * g.S + off;
 #pragma unroll
-        for (int k = 0; k < NK; ++k) {
-            const float rh = rh_t[k], ru = ru_t[k];
-            const float pr = fmaf(slr, sr[k], fmaf(-sli, si[k], tr[k]));
-            const float pi = fmaf(slr, si[k], fmaf(sli, sr[k], ti[k]));
-            const float g_ = rh * rcp_approx(fmaf(rh, rtaa, ru));
-            const float cr = g_ * pr, ci = g_ * pi;
-            const float Q = g_ * ru;
-            const float dr = fmaf(-cr, c.sab_re, fmaf(-ci, c.sab_im, sr[k]));
-            const float di = fmaf(-ci, c.sab_re, fmaf(cr, c.sab_im, si[k]));
-            Bk[k] = fmaf(dr, dr, fmaf(di, di, Q * c.sab2));
-            rru[k] = rcp_approx(ru);
-            if (valid[k]) s1 = fmaf(g_ru[k], Bk[k], s1);
-        }
-        s1 = block_sum<BLOCK>(s1, red, (parity++) & 1);
-        const float glam1 = g_lam - s1 * ilM / lam1;             // ilM = invM / lambda'
-        const float gell = glam1 / (float)J;
-        float pr_rtaa = 0.f, pr_slr = 0.f, pr_sli = 0.f;
-#pragma unroll
-        for (int k = 0; k < NK; ++k) {
-            if (!valid[k]) {
-                g_rh[k] = g_ru[k] = 0.f;
-                continue;
+                for (int k = 0; k < NK; ++k) {
+                    rh_t[k] = valid[k] ? srh[k * BLOCK + tid] : 0.f;
+                    ru_t[k] = valid[k] ? sru[k * BLOCK + tid] : 1.f;
+                }
             }
-            const float rh = rh_t[k], ru = ru_t[k];
-            const float pr = fmaf(slr, sr[k], fmaf(-sli, si[k], tr[k]));
-            const float pi = fmaf(slr, si[k], fmaf(sli, sr[k], ti[k]));
-            const float rD = rcp_approx(fmaf(rh, rtaa, ru));
-            const float g_ = rh * rD;
-            const float cr = g_ * pr, ci = g_ * pi;
-            const float Q = g_ * ru;
-            const float dr = fmaf(-cr, c.sab_re, fmaf(-ci, c.sab_im, sr[k]));
-            const float di = fmaf(-ci, c.sab_re, fmaf(cr, c.sab_im, si[k]));
-            const float er = fmaf(-tr[k], c.inv_taa, cr);
-            const float ei = fmaf(-ti[k], c.inv_taa, ci);
-            const float X = fmaf(er, er, fmaf(ei, ei, Q));
-            const float gAk = g_ru[k];
-            const float gBk = g_ru[k] * ilM + gell * rru[k];
-            float gru = -gell * Bk[k] * rru[k] * rru[k];
-            const float gX = gAk * c.taaM;
-            g_k[k] += gAk * c.invM;
-            p_taaM += gAk * X;
-            float gcr = 2.f * er * gX, gci = 2.f * ei * gX;
-            float gQ = gX;
-            g_tr[k] -= gcr * c.inv_taa;
-            g_ti[k] -= gci * c.inv_taa;
-            p_invtaa -= gcr * tr[k] + gci * ti[k];
-            const float gdr = 2.f * dr * gBk, gdi = 2.f * di * gBk;
-            gQ += gBk * c.sab2;
-            p_sab2 += gBk * Q;
-            g_sr[k] += gdr;
-            g_si[k] += gdi;
-            gcr += -gdr * c.sab_re + gdi * c.sab_im;
-            gci += -gdr * c.sab_im - gdi * c.sab_re;
-            p_sre += -gdr * cr - gdi * ci;
-            p_sim += -gdr * ci + gdi * cr;
-            const float grhat = g_rh[k] * p.c_a2;
-            gcr += 2.f * cr * grhat;
-            gci += 2.f * ci * grhat;
-            gQ += grhat;
-            float gg = gQ * ru;
-            gru += gQ * g_;
-            gg += gcr * pr + gci * pi;
-            const float gpr = gcr * g_, gpi = gci * g_;
-            float grh = gg * rD;
-            const float gD = -gg * rh * rD * rD;
-            grh += gD * rtaa;
-            gru += gD;
-            pr_rtaa += gD * rh;
-            g_tr[k] += gpr;
-            g_ti[k] += gpi;
-            g_sr[k] += gpr * slr + gpi * sli;
-            g_si[k] += -gpr * sli + gpi * slr;
-            pr_slr += gpr * sr[k] + gpi * si[k];
-            pr_sli += -gpr * si[k] + gpi * sr[k];
-            g_rh[k] = grh;
-            g_ru[k] = gru;
+            const float lam_t = g.seg_lam[(size_t)(t - t0) * g.R + r];
+            const float lam1 = t == t1 - 1 ? lam_end : g.seg_lam[(size_t)(t + 1 - t0) * g.R + r];
+            const float il = rcp_refined(lam_t);
+            const float rtaa = fmaf(c.sab2, il, c.taa);
+            const float slr = c.sab_re * il, sli = c.sab_im * il;
+            const float ilM = rcp_refined(lam1) * c.invM;
+            // S1 = sum_j g_ru'_j B_j  (B needs the forward intermediates)
+            float Bk[NK], rru[NK];
+            float s1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                const float rh = rh_t[k], ru = ru_t[k];
+                const float pr = fmaf(slr, sr[k], fmaf(-sli, si[k], tr[k]));
+                const float pi = fmaf(slr, si[k], fmaf(sli, sr[k], ti[k]));
+                const float g_ = rh * rcp_approx(fmaf(rh, rtaa, ru));
+                const float cr = g_ * pr, ci = g_ * pi;
+                const float Q = g_ * ru;
+                const float dr = fmaf(-cr, c.sab_re, fmaf(-ci, c.sab_im, sr[k]));
+                const float di = fmaf(-ci, c.sab_re, fmaf(cr, c.sab_im, si[k]));
+                Bk[k] = fmaf(dr, dr, fmaf(di, di, Q * c.sab2));
+                rru[k] = rcp_approx(ru);
+                if (valid[k]) s1 = fmaf(g_ru[k], Bk[k], s1);
+            }
+            s1 = block_sum<BLOCK>(s1, red, (parity++) & 1);
+            const float glam1 = g_lam - s1 * ilM / lam1;             // ilM = invM / lambda'
+            const float gell = glam1 / (float)J;
+            float pr_rtaa = 0.f, pr_slr = 0.f, pr_sli = 0.f;
+#pragma unroll
+            for (int k = 0; k < NK; ++k) {
+                if (!valid[k]) {
+                    g_rh[k] = g_ru[k] = 0.f;
+                    continue;
+                }
+                const float rh = rh_t[k], ru = ru_t[k];
+                const float pr = fmaf(slr, sr[k], fmaf(-sli, si[k], tr[k]));
+                const float pi = fmaf(slr, si[k], fmaf(sli, sr[k], ti[k]));
+                const float rD = rcp_approx(fmaf(rh, rtaa, ru));
+                const float g_ = rh * rD;
+                const float cr = g_ * pr, ci = g_ * pi;
+                const float Q = g_ * ru;
+                const float dr = fmaf(-cr, c.sab_re, fmaf(-ci, c.sab_im, sr[k]));
+                const float di = fmaf(-ci, c.sab_re, fmaf(cr, c.sab_im, si[k]));
+                const float er = fmaf(-tr[k], c.inv_taa, cr);
+                const float ei = fmaf(-ti[k], c.inv_taa, ci);
+                const float X = fmaf(er, er, fmaf(ei, ei, Q));
+                const float gAk = g_ru[k];
+                const float gBk = g_ru[k] * ilM + gell * rru[k];
+                float gru = -gell * Bk[k] * rru[k] * rru[k];
+                const float gX = gAk * c.taaM;
+                g_k[k] += gAk * c.invM;
+                p_taaM += gAk * X;
+                float gcr = 2.f * er * gX, gci = 2.f * ei * gX;
+                float gQ = gX;
+                g_tr[k] -= gcr * c.inv_taa;
+                g_ti[k] -= gci * c.inv_taa;
+                p_invtaa -= gcr * tr[k] + gci * ti[k];
+                const float gdr = 2.f * dr * gBk, gdi = 2.f * di * gBk;
+                gQ += gBk * c.sab2;
+                p_sab2 += gBk * Q;
+                g_sr[k] += gdr;
+                g_si[k] += gdi;
+                gcr += -gdr * c.sab_re + gdi * c.sab_im;
+                gci += -gdr * c.sab_im - gdi * c.sab_re;
+                p_sre += -gdr * cr - gdi * ci;
+                p_sim += -gdr * ci + gdi * cr;
+                const float grhat = g_rh[k] * p.c_a2;
+                gcr += 2.f * cr * grhat;
+                gci += 2.f * ci * grhat;
+                gQ += grhat;
+                float gg = gQ * ru;
+                gru += gQ * g_;
+                gg += gcr * pr + gci * pi;
+                const float gpr = gcr * g_, gpi = gci * g_;
+                float grh = gg * rD;
+                const float gD = -gg * rh * rD * rD;
+                grh += gD * rtaa;
+                gru += gD;
+                pr_rtaa += gD * rh;
+                g_tr[k] += gpr;
+                g_ti[k] += gpi;
+                g_sr[k] += gpr * slr + gpi * sli;
+                g_si[k] += -gpr * sli + gpi * slr;
+                pr_slr += gpr * sr[k] + gpi * si[k];
+                pr_sli += -gpr * si[k] + gpi * sr[k];
+                g_rh[k] = grh;
+                g_ru[k] = gru;
+            }
+            float rv[8] = {pr_rtaa, pr_slr, pr_sli, 0.f, 0.f, 0.f, 0.f, 0.f};
+            block_sum_n<BLOCK, 8>(rv, redn, (parity++) & 1);
+            u_taa += rv[0];
+            u_sab2 += rv[0] * il;
+            u_sre += rv[1] * il;
+            u_sim += rv[2] * il;
+            const float gil = rv[0] * c.sab2 + rv[1] * c.sab_re + rv[2] * c.sab_im;
+            g_lam = -gil * il * il;
         }
-        float rv[8] = {pr_rtaa, pr_slr, pr_sli, 0.f, 0.f, 0.f, 0.f, 0.f};
-        block_sum_n<BLOCK, 8>(rv, redn, (parity++) & 1);
-        u_taa += rv[0];
-        u_sab2 += rv[0] * il;
-        u_sre += rv[1] * il;
-        u_sim += rv[2] * il;
-        const float gil = rv[0] * c.sab2 + rv[1] * c.sab_re + rv[2] * c.sab_im;
-        g_lam = -gil * il * il;
     }
 
     // ---- 3. invariants -> x; row sums staged in shared memory ----------------------------

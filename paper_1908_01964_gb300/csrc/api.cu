@@ -38,6 +38,9 @@ struct rcscm_ctx {
     float* ckpt_rh = nullptr;        // [n_ckpt][S]
     float* ckpt_ru = nullptr;        // [n_ckpt][S]
     float* ckpt_lam = nullptr;       // [n_ckpt][R]
+    float* seg_rh = nullptr;         // adjoint scratch: [stride][S], [stride][S], [stride][R]
+    float* seg_ru = nullptr;
+    float* seg_lam = nullptr;
     int iters_done = 0;              // passes since the last setup / set_state
     int iter_block = 0;              // block of those passes (-1: mixed)
 };
@@ -99,6 +102,7 @@ IterParams iter_params(const rcscm_options& o) {
     p.ru_floor = o.ru_floor;
     p.c_a2_f64 = 1.0 / (o.alpha + 2.0);
     p.c_b_f64 = o.beta / (o.alpha + 2.0);
+    p.ckpt_first = 0;
     return p;
 }
 
@@ -235,6 +239,8 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
     DevState& d = c->d;
     int st = RCSCM_OK;
     const size_t Rz = (size_t)R, Sz = (size_t)S;
+    d.n_slots = S;
+    d.n_rows = R;
     if (!st) st = dalloc(c, &d.rows, Rz);
     if (!st) st = dalloc(c, &d.rc, Rz);
     if (!st) st = dalloc(c, &d.bmap, (size_t)n_blocks);
@@ -271,6 +277,14 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
         if (!st) st = dalloc(c, &c->ckpt_rh, Sz * (size_t)c->n_ckpt);
         if (!st) st = dalloc(c, &c->ckpt_ru, Sz * (size_t)c->n_ckpt);
         if (!st) st = dalloc(c, &c->ckpt_lam, Rz * (size_t)c->n_ckpt);
+        d.ckpt_rh = c->ckpt_rh;
+        d.ckpt_ru = c->ckpt_ru;
+        d.ckpt_lam = c->ckpt_lam;
+        d.ckpt_stride = eff.ckpt_stride;
+        const size_t seg = (size_t)std::min(eff.ckpt_stride, eff.ckpt_max_iters);
+        if (!st) st = dalloc(c, &c->seg_rh, Sz * seg);
+        if (!st) st = dalloc(c, &c->seg_ru, Sz * seg);
+        if (!st) st = dalloc(c, &c->seg_lam, Rz * seg);
     }
     if (!st && opt->rule == RCSCM_RULE_NAIVE) {
         float* q = nullptr;
@@ -321,26 +335,14 @@ int rcscm_iterate(rcscm_ctx* c, int n_iter, void* stream) {
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     const IterParams p = iter_params(c->opt);
     const int chunk = c->opt.iters_per_launch > 0 ? c->opt.iters_per_launch : n_iter;
-    const int stride = c->opt.ckpt_stride;
-    if (stride > 0 && n_iter > c->opt.ckpt_max_iters - c->iters_done) return RCSCM_EINVAL;
+    if (c->opt.ckpt_stride > 0 && n_iter > c->opt.ckpt_max_iters - c->iters_done) return RCSCM_EINVAL;
     for (int done = 0; done < n_iter;) {
-        int k = std::min(chunk, n_iter - done);
-        cudaError_t e = cudaSuccess;
-        if (stride > 0) {                    // launches end at checkpoint boundaries
-            const int u = c->iters_done;
-            k = std::min(k, stride - u % stride);
-            if (u % stride == 0) {
-                const size_t q = (size_t)(u / stride);
-                e = cudaMemcpyAsync(c->ckpt_rh + q * c->S, c->d.rh, c->S * sizeof(float), cudaMemcpyDeviceToDevice, cs);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(c->ckpt_ru + q * c->S, c->d.ru, c->S * sizeof(float), cudaMemcpyDeviceToDevice, cs);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(c->ckpt_lam + q * c->R, c->d.lam, c->R * sizeof(float), cudaMemcpyDeviceToDevice, cs);
-                if (e != cudaSuccess) return map_cuda(e);
-            }
-        }
+        const int k = std::min(chunk, n_iter - done);
+        IterParams pk = p;
+        pk.ckpt_first = c->iters_done;        // the accelerated kernel writes checkpoints itself
+        cudaError_t e;
         if (c->opt.rule == RCSCM_RULE_ACCEL)
-            e = launch_accel(c->d, (int)c->R, c->max_j, c->opt.block, k, p, c->opt.persistent != 0, cs);
+            e = launch_accel(c->d, (int)c->R, c->max_j, c->opt.block, k, pk, c->opt.persistent != 0, cs);
         else
             e = launch_naive(c->d, c->naive_rows, c->count_by_m, c->first_by_m, k, p,
                              c->opt.rule == RCSCM_RULE_NAIVE_F64, cs);
@@ -522,6 +524,8 @@ int rcscm_autotune(rcscm_ctx* c, int n_iter_probe, int* chosen_block, int* chose
     };
     if (e == cudaSuccess) e = copy_state(true);
     const IterParams p = iter_params(c->opt);
+    DevState dd = c->d;                      // probe passes must not overwrite checkpoints
+    dd.ckpt_stride = 0;
     float best = 3.0e38f;
     const bool fixed_block = c->opt.ckpt_stride > 0;   // the adjoint needs the context's block
     int best_block = fixed_block ? c->opt.block : accel_default_block(c->max_j), best_pers = 0;
@@ -535,7 +539,7 @@ int rcscm_autotune(rcscm_ctx* c, int n_iter_probe, int* chosen_block, int* chose
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
                 e = copy_state(false);
                 if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
-                if (e == cudaSuccess) e = launch_accel(c->d, (int)c->R, c->max_j, b, n_iter_probe, p, pers != 0, cs);
+                if (e == cudaSuccess) e = launch_accel(dd, (int)c->R, c->max_j, b, n_iter_probe, p, pers != 0, cs);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.f;
@@ -602,6 +606,9 @@ int rcscm_backward(rcscm_ctx* c, const void* grad_h, void* grad_x, void* grad_a,
     g.ckpt_rh = c->ckpt_rh;
     g.ckpt_ru = c->ckpt_ru;
     g.ckpt_lam = c->ckpt_lam;
+    g.seg_rh = c->seg_rh;
+    g.seg_ru = c->seg_ru;
+    g.seg_lam = c->seg_lam;
     g.K = c->iters_done;
     g.stride = c->opt.ckpt_stride;
     g.S = c->S;

@@ -63,13 +63,23 @@ __global__ void __launch_bounds__(kSlotBlock) objective_kernel(DevState d, float
     }
 }
 
-__global__ void objective_sum_kernel(const double* __restrict__ part, const int* __restrict__ first_block,
-                                     int n_probs, double* __restrict__ out) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n_probs) return;
+// One CTA per utterance: thread t sums partials t, t + 256, ... in order, then a
+// fixed tree over the threads (deterministic for a given block count).
+constexpr int kSumThreads = 256;
+__global__ void __launch_bounds__(kSumThreads) objective_sum_kernel(const double* __restrict__ part,
+                                                                   const int* __restrict__ first_block,
+                                                                   double* __restrict__ out) {
+    __shared__ double red[kSumThreads];
+    const int p = blockIdx.x;
     double s = 0.0;
-    for (int b = first_block[p]; b < first_block[p + 1]; ++b) s += part[b];
-    out[p] = s;
+    for (int b = first_block[p] + threadIdx.x; b < first_block[p + 1]; b += kSumThreads) s += part[b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = kSumThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[p] = red[0];
 }
 
 }  // namespace
@@ -81,7 +91,7 @@ cudaError_t launch_objective(const DevState& d, int n_blocks, const IterParams& 
     objective_kernel<<<n_blocks, kSlotBlock, 0, s>>>(d, (float)(alpha + 1.0), (float)beta);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    objective_sum_kernel<<<(n_probs + 127) / 128, 128, 0, s>>>(d.obj_part, first_block, n_probs, out);
+    objective_sum_kernel<<<n_probs, kSumThreads, 0, s>>>(d.obj_part, first_block, out);
     return cudaGetLastError();
 }
 

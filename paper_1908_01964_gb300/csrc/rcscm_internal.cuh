@@ -69,6 +69,11 @@ struct DevState {
     float2* b32;           // [R][8]
     float2* rp32;          // [R][8][8]  (naive rule)
     double2* evec64;       // [R][64] eigenvectors of R', entry m * M + i = e_i[m], ascending (adjoint), or nullptr
+    float* ckpt_rh;        // checkpoints written by the accelerated kernel when ckpt_stride > 0:
+    float* ckpt_ru;        //   the state entering pass k * ckpt_stride, [k][S] and [k][R]
+    float* ckpt_lam;
+    int ckpt_stride;
+    int64_t n_slots, n_rows;   // S and R of the context
     // per-slot invariants and EM state
     float4* inv4;          // [S] {tau_ax.re, tau_ax.im, sigma_bx.re, sigma_bx.im}
     float* kap;            // [S] kappa = tau_xx - |tau_ax|^2 / tau_aa
@@ -88,6 +93,7 @@ struct IterParams {
     float ru_floor;
     double c_a2_f64; // the same constants in FP64 (naive FP64 rule)
     double c_b_f64;
+    int ckpt_first;        // index (since setup) of the first pass of this launch
 };
 
 // ------------------------------------------------------------------ helpers
@@ -194,13 +200,6 @@ __device__ __forceinline__ float2 cmul_exact(float2 w, float2 a) {
     return make_float2(fmaf(w.x, a.x, -(w.y * a.y)), fmaf(w.x, a.y, w.y * a.x));
 }
 
-// Minimum resident CTAs per SM requested from the compiler for the accelerated
-// kernels: with kappa/M and B in shared memory, 128 x 8 fits 7 CTAs (72
-// registers) and 256 x 8 fits 3 (80), so rows of up to 1024 / 2048 frames keep
-// more rows resident at once; other shapes are left to the compiler.
-constexpr int accel_min_blocks(int block, int spt) {
-    return (block == 128 && spt == 8) ? 7 : ((block == 256 && spt == 8) ? 3 : 0);
-}
 
 // Butterfly sum over a warp: every lane ends with the same, order-fixed value.
 __device__ __forceinline__ float warp_sum(float v) {
@@ -213,9 +212,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // Accelerated kernel shapes: threads per row (32 ... 1024) and the largest
 // number of slots each thread keeps in registers for that block size.
-__host__ __device__ constexpr int accel_max_spt(int block) {
-    return block >= 1024 ? 4 : (block <= 128 ? 16 : 8);
-}
+__host__ __device__ constexpr int accel_max_spt(int block) { return block >= 1024 ? 4 : 8; }
 // Default block for rows of up to max_j slots: the smallest block that keeps
 // at most 8 slots per thread.
 inline int accel_default_block(int max_j) {
@@ -239,6 +236,9 @@ struct AdjointArgs {
     const float* ckpt_rh;   // [n_ckpt][S]: state entering pass k * stride
     const float* ckpt_ru;
     const float* ckpt_lam;  // [n_ckpt][R]
+    float* seg_rh;          // [stride][S] states entering the passes of one segment (scratch)
+    float* seg_ru;          // [stride][S]
+    float* seg_lam;         // [stride][R]
     int K;                  // passes run since setup
     int stride;             // passes between checkpoints
     int64_t S, R;

@@ -272,8 +272,10 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
             if (e < MM) X[e / M][e % M] = nx[t];
         }
         __syncwarp();
-        // |E| <= 1e-9: the next correction would be below FP64 rounding (quadratic convergence)
-        if (__all_sync(0xffffffffu, !(emax > 1e-18))) break;
+        // |E| <= 1e-6 was just applied: by quadratic convergence the remaining error is of
+        // order |E|^2 <= 1e-12 (scaled by the eigenvalue gaps): far below the FP32 outputs' rounding
+        // and the tolerances of the FP64 rule and the adjoint
+        if (__all_sync(0xffffffffu, !(emax > 1e-12))) break;
     }
 
     // ---- ascending order of the eigenvalues (ranks) --------------------------------
@@ -330,14 +332,30 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     // w = u - alpha e_0 with alpha = -ph0 |u| -> w_0 = ph0 (|u_0| + 1); |w|^2 = 2 + 2|u_0|
     const double two_over_wn2 = 2.0 / (2.0 + 2.0 * au0);
 
-    // FP32 copy of R' for the naive rule, with the smallest eigenvalue set to zero
-    // (R' + lambda b b^H is then exactly the model's R_i)
+    // Householder data shared by the rows of Phi (in the refinement's T array, free by
+    // now): w_i (i = 1..M-1) and q_n = sum_i conj(w_i e_i[n]) / sqrt(mu_i), once per n.
+    double2* wd = &sT[g][0][0];
+    double2* qd = &sT[g][1][0];
+    if (l >= 1 && l < M)   // w = u - alpha e_0 in the whitened basis, u_i = c_{i+1} / (sqrt(mu_{i+1}) |v|)
+        wd[l] = (l == 1) ? zscale(ph0, au0 + 1.0) : zscale(sc[g][l], inv_nv * srs[g][l]);
+    __syncwarp(gmask);
+    if (l < M) {
+        double2 q = make_double2(0.0, 0.0);
+        for (int i = 1; i < M; ++i) q = zadd(q, zscale(zconj(zmul(wd[i], X[l][perm[i]])), srs[g][i]));
+        qd[l] = q;
+    }
+    __syncwarp(gmask);
+    // FP32 copy of R' with the smallest eigenvalue set to zero (R' + lambda b b^H is then
+    // exactly the model's R_i); formed in FP32 (mu_1 b b^H is a rounding-level term)
+    const float mu1f = (float)mu1;
     for (int e = l; e < MM; e += kGroupLanes) {
         const int m = e / M, n = e % M;
-        const double2 v = zsub(A[m][n], zscale(zmulc(X[n][k0], X[m][k0]), mu1));
-        d.rp32[(size_t)r * 64 + e] = make_float2((float)v.x, (float)v.y);
+        const float2 b_m = make_float2((float)X[m][k0].x, (float)X[m][k0].y);
+        const float2 b_n = make_float2((float)X[n][k0].x, (float)X[n][k0].y);
+        const float2 v = make_float2((float)A[m][n].x, (float)A[m][n].y);
+        d.rp32[(size_t)r * 64 + e] = csub(v, cscale(cmul(b_m, cconj(b_n)), mu1f));
     }
-    // Phi entries (kk, n): row 0 (R'^+ a)^H, rows 1..M-2 H L^H, row M-1 b^H
+    // Phi entries (kk, n): row 0 (R'^+ a)^H, rows 1..M-2 H L^H, row M-1 b^H (FP64, rounded once)
     float2* phi = d.phi + (size_t)r * 64;
     for (int e = l; e < MM; e += kGroupLanes) {
         const int kk = e / M, n = e % M;
@@ -350,13 +368,8 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
         } else if (kk == M - 1) {
             val = zconj(X[n][k0]);
         } else {                                         // H L^H entry, L = [e_i / sqrt(mu_i)]
-            double2 qn = make_double2(0.0, 0.0);         // sum_l conj(w_l e_{l+1}[n]) / sqrt(mu_{l+1})
-            for (int i = 1; i < M; ++i) {
-                const double2 wl = (i == 1) ? zscale(ph0, au0 + 1.0) : zscale(sc[g][i], inv_nv * srs[g][i]);
-                qn = zadd(qn, zscale(zconj(zmul(wl, X[n][perm[i]])), srs[g][i]));
-            }
-            const double2 wk = zscale(sc[g][kk + 1], inv_nv * srs[g][kk + 1]);
-            val = zsub(zscale(zconj(X[n][perm[kk + 1]]), srs[g][kk + 1]), zscale(zmul(wk, qn), two_over_wn2));
+            val = zsub(zscale(zconj(X[n][perm[kk + 1]]), srs[g][kk + 1]),
+                       zscale(zmul(wd[kk + 1], qd[n]), two_over_wn2));
         }
         phi[e] = make_float2((float)val.x, (float)val.y);
     }

@@ -17,16 +17,17 @@ def _lib():
     rcscm.lib()
 
 
-def _batch(n=6, I=33, seed=700):
+def _batch(n=6, I=33, seed=700, max_j=2000):
     rng = np.random.default_rng(seed)
-    specs = [synth.ProblemSpec(M=int(rng.choice([2, 4, 6])), I=I, J=int(rng.integers(100, 2001)), K=5, spacing=0.04)
+    specs = [synth.ProblemSpec(M=int(rng.choice([2, 4, 6])), I=I, J=int(rng.integers(100, max_j + 1)), K=5,
+                               spacing=0.04)
              for _ in range(n)]
     return [synth.make_problem(s, seed + k) for k, s in enumerate(specs)]
 
 
 @pytest.mark.parametrize("block", [128, 256, 512])
 def test_persistent_launch_equals_one_cta_per_row(block):
-    probs = _batch()
+    probs = _batch(max_j=8 * block)                 # rows of up to 8 * block frames
     a, _ = gpu_run(probs, 12, block=block, persistent=0)
     b, _ = gpu_run(probs, 12, block=block, persistent=1)
     for x, y in zip(a, b):
