@@ -159,6 +159,7 @@ def load_peaks():
 KERNEL_SOURCES = {
     "accel_kernel": ["accel_common.cuh", "iterate_impl.cuh", "rcscm_internal.cuh"],
     "solve_kernel": ["accel_common.cuh", "iterate_impl.cuh", "rcscm_internal.cuh"],
+    "accel_stream_kernel": ["accel_common.cuh", "stream_kernel.cuh", "rcscm_internal.cuh"],
     "setup_kernel": ["setup.cu", "rcscm_internal.cuh"],
     "naive_kernel": ["naive.cu", "rcscm_internal.cuh"],
     "adjoint_kernel": ["accel_common.cuh", "adjoint.cu", "rcscm_internal.cuh"],
@@ -249,16 +250,43 @@ def choose_sample_rows(p, n_iter, target_s):
     return np.linspace(0, I - 1, n).round().astype(int)
 
 
-def cpu_baseline(p, wl, rule):
+def _oracle_rows(job):
+    """Pool worker: the oracle on one block of rows; returns its wall time."""
+    prob, n_iter, rule = job
     from oracle import rcscm_oracle as O
-    rows = choose_sample_rows(p, wl.n_iter, target_s=15.0)
+    t0 = time.perf_counter()
+    O.run(prob, n_iter, "accel2" if rule == "accel" else "naive")
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(p, wl, rule):
+    """The FP64 oracle on the host: one core on a sample of rows, and every core
+    (a spawn-started process pool over contiguous blocks of rows; rows are
+    independent) on the whole utterance."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from oracle import rcscm_oracle as O
+    rows = choose_sample_rows(p, wl.n_iter, target_s=10.0)
     c0, t0 = time.process_time(), time.perf_counter()
     O.run(p, wl.n_iter, "accel2" if rule == "accel" else "naive", rows=rows)
     dt, dc = time.perf_counter() - t0, time.process_time() - c0
-    J = p["x"].shape[1]
-    return {"value": len(rows) * J * wl.n_iter / dt, "unit": UNIT, "cores": max(1, round(dc / dt)), "kind": "oracle",
-            "sample": f"{len(rows)} of {p['x'].shape[0]} rows x J={J} x {wl.n_iter} iterations of {wl.name} "
-                      f"(setup + invariants + iterations + Wiener), numpy FP64, {dt:.1f} s"}
+    I, J = p["x"].shape[0], p["x"].shape[1]
+    single = {"value": len(rows) * J * wl.n_iter / dt, "unit": UNIT, "cores": max(1, round(dc / dt)),
+              "sample": f"{len(rows)} of {I} rows x J={J} x {wl.n_iter} iterations of {wl.name}, {dt:.1f} s"}
+    n = max(1, min(os.cpu_count() or 1, I))
+    keys = ("x", "a", "Rp", "rh0", "ru0")
+    bounds = np.linspace(0, I, n + 1).round().astype(int)
+    jobs = [({k: np.ascontiguousarray(p[k][bounds[w]:bounds[w + 1]]) for k in keys}, wl.n_iter, rule)
+            for w in range(n) if bounds[w + 1] > bounds[w]]
+    with cf.ProcessPoolExecutor(len(jobs), mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_rows, [({k: v[:1] for k, v in jobs[0][0].items()}, 1, rule)] * len(jobs)))  # warm
+        t0 = time.perf_counter()
+        list(ex.map(_oracle_rows, jobs))
+        dtp = time.perf_counter() - t0
+    return {"value": I * J * wl.n_iter / dtp, "unit": UNIT, "cores": len(jobs), "kind": "oracle",
+            "sample": f"all {I} rows x J={J} x {wl.n_iter} iterations of {wl.name} (setup + invariants + "
+                      f"iterations + Wiener), numpy FP64, {len(jobs)} processes over row blocks, {dtp:.2f} s",
+            "single_core": single}
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -430,11 +458,12 @@ def run_ours(args):
         bytes_ = ACCEL_BYTES_PER_SLOT_LAUNCH * slots
         achieved = bytes_ / (launch_ms / 1e3) / 1e9
         peak = float(peaks.get("hbm_gbs", 6800.0))
-        traffic, tsrc = profiled_traffic("accel_kernel", f"{wl.name}-x{args.replicas}-streaming")
+        kname = "accel_stream_kernel" if iters_per_launch == 1 and not args.persistent else "accel_kernel"
+        traffic, tsrc = profiled_traffic(kname, f"{wl.name}-x{args.replicas}-streaming")
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": traffic, "traffic_source": tsrc, "traffic_algorithmic": bytes_,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback",
-                    "kernel": f"accel_kernel (streaming, {iters_per_launch} iteration(s) per launch)",
+                    "kernel": f"{kname} ({iters_per_launch} iteration(s) per launch)",
                     "algorithmic": f"{ACCEL_BYTES_PER_SLOT_LAUNCH} B per slot per launch"}
     else:
         roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
@@ -525,6 +554,7 @@ def streaming_roofline(args, R, dev, peaks, stream, reuse=None):
     s = R.Solver(copies, rule="accel", iters_per_launch=1, block=args.block)
     slots = s.info()["slots"]
     s.setup()
+    shape = s.autotune(n_iter_probe=1) if args.block == 0 else (args.block, 0)
     for _ in range(5):
         s.iterate(1)
     n = args.streaming_launches
@@ -542,14 +572,15 @@ def streaming_roofline(args, R, dev, peaks, stream, reuse=None):
     bytes_ = ACCEL_BYTES_PER_SLOT_LAUNCH * slots
     achieved = bytes_ / (t / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    traffic, tsrc = profiled_traffic("accel_kernel", f"{wl.name}-x{args.streaming_replicas}-streaming")
+    traffic, tsrc = profiled_traffic("accel_stream_kernel", f"{wl.name}-x{args.streaming_replicas}-streaming")
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_source": tsrc, "traffic_algorithmic": bytes_,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured burst copy)" if peaks else "fallback 6800 GB/s",
-            "kernel": "accel_kernel, 1 pass per launch",
+            "kernel": "accel_stream_kernel (1 pass per launch)",
             "workload": f"{wl.name}" + (f" x{args.streaming_replicas}" if args.streaming_replicas > 1 else "")
                         + f", {slots} slots, {bytes_ / 1e6:.0f} MB per launch (invariants + state > L2)",
             "launch_us_median": 1e3 * t, "launches": n, "slot_updates_per_s": slots / (t / 1e3),
+            "shape": {"block": shape[0], "persistent": shape[1], "autotuned": args.block == 0},
             "status": R.strerror(code)}
 
 

@@ -19,7 +19,7 @@
 //      g_x = P a g_tau + 2 g_txx P x + b g_sigma per slot, and the row sums
 //      v_a = sum_j x_j conj(g_tau_j), v_b = sum_j x_j conj(g_sigma_j),
 //      C = sum_j g_txx_j x_j x_j^H, staged through shared memory and added in
-//      FP64 in slot order.
+//      slot order with compensated FP32 sums.
 //   4. Setup (FP64, warp 0, entry-parallel), in the eigenbasis E of R' (mu_1 <
 //      mu_2 <= ...; b = e_1; P = sum_{i>=2} e_i e_i^H / mu_i).  With G the
 //      Hermitian gradient of P and g_b that of b (every use: tau_aa = a^H P a,
@@ -55,6 +55,15 @@ __device__ __forceinline__ void block_sum_n(float (&v)[N], float (*red)[BLOCK / 
         for (int w = 0; w < NW; ++w) t += red[parity][w][i];
         v[i] = t;
     }
+}
+
+// s += v with Kahan compensation c (s + (-c) tracks the exact running sum).  The
+// compiler does not reassociate these operations (no fast-math).
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
 }
 
 constexpr int kStage = 2 * kMaxM + 5;                     // x (2M) + g_tau (2) + g_sigma (2) + g_txx
@@ -347,9 +356,11 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     // kappa = tau_xx - |tau_ax|^2 / tau_aa: its tau_ax part joins g_tau (where it largely
     // cancels the pass's own tau_ax gradient) and its tau_aa part joins p_taa.  Roles of
     // the summing threads: C = sum g_txx x x^H (M*M), v_a = sum x conj(g_tau) (M),
-    // v_b = sum x conj(g_sigma) (M); every term is added in FP64, in slot order (these
-    // sums cancel heavily in step 4, so FP32 accumulation would lose the result).
-    double2 acc = make_double2(0.0, 0.0);
+    // v_b = sum x conj(g_sigma) (M), each accumulated in slot order with compensated
+    // (Kahan) FP32 sums: they cancel heavily in step 4, so plain FP32 accumulation would
+    // lose the result, and the compensated sum keeps it at the rounding of the terms
+    // without the cost of FP64 (on sm_103a FP64 runs at a small fraction of the FP32 rate).
+    float2 acc = make_float2(0.f, 0.f), comp = make_float2(0.f, 0.f);
     const int n_roles = MM + 2 * M;
     for (int k = 0; k < NK; ++k) {
         const int j = k * BLOCK + tid;
@@ -397,8 +408,8 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
                     term = cmul(make_float2(o[2 * m], o[2 * m + 1]),
                                 make_float2(o[2 * kMaxM + q], -o[2 * kMaxM + q + 1]));
                 }
-                acc.x += (double)term.x;
-                acc.y += (double)term.y;
+                kahan_add(acc.x, comp.x, term.x);
+                kahan_add(acc.y, comp.y, term.y);
             }
         }
         __syncthreads();
@@ -408,9 +419,10 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     block_sum_n<BLOCK, 8>(pv, redn, (parity++) & 1);
 
     // ---- 4. setup adjoint in FP64 (warp 0) -----------------------------------------------
-    if (tid < MM) dG[tid / M][tid % M] = acc;
-    else if (tid < MM + M) dva[tid - MM] = acc;
-    else if (tid < n_roles) dvb[tid - MM - M] = acc;
+    const double2 accd = make_double2((double)acc.x - (double)comp.x, (double)acc.y - (double)comp.y);
+    if (tid < MM) dG[tid / M][tid % M] = accd;
+    else if (tid < MM + M) dva[tid - MM] = accd;
+    else if (tid < n_roles) dvb[tid - MM - M] = accd;
     __syncthreads();
     if (tid >= 32) return;
     const int lane = tid;

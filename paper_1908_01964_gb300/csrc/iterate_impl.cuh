@@ -121,73 +121,7 @@ __global__ void __launch_bounds__(BLOCK, solve_min_blocks(BLOCK, SPT)) solve_ker
     accel_one_row<BLOCK, SPT, true>(d, d.order[blockIdx.x], n_iter, p, red, h, &fs);
 }
 
-// Streaming form of a launch that runs exactly one pass: the row's pairs are
-// loaded, updated and stored one at a time, with A/M and B of pass A kept in
-// shared memory for pass B, so few registers are live and several rows stream
-// through each SM.  Same operations in the same order and the same reduction as
-// the register-resident form, so the results are bitwise equal.
-template <int BLOCK, int SPT>
-__global__ void __launch_bounds__(BLOCK) accel_stream_kernel(DevState d, IterParams p) {
-    __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
-    __shared__ f32x2 s_am[SPT / 2][BLOCK], s_b[SPT / 2][BLOCK];
-    const int r = d.order[blockIdx.x];
-    const RowDesc* rd = d.rows + r;
-    const int J = rd->J;
-    const int64_t off = rd->slot_off;
-    const RowConst c = d.rc[r];
-    const int tid = threadIdx.x;
-    const int np = (J + 2 * BLOCK - 1) / (2 * BLOCK);     // 1..SPT/2 (checked by the host)
-    const float lam0 = d.lam[r];
-    const bool ckpt = d.ckpt_stride > 0 && p.ckpt_first % d.ckpt_stride == 0;
-    const size_t kc = ckpt ? (size_t)(p.ckpt_first / d.ckpt_stride) : 0;
-    const PassConsts k = pass_consts(c, p, lam0);
-    f32x2 part = dup(0.f);
-    for (int q = 0; q < np; ++q) {
-        const int j0 = 2 * q * BLOCK + tid, j1 = j0 + BLOCK;
-        const bool v0 = j0 < J, v1 = j1 < J;
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 t0 = v0 ? d.inv4[off + j0] : z, t1 = v1 ? d.inv4[off + j1] : z;
-        const float km0 = v0 ? fmaf(d.kap[off + j0], c.invM, p.ru_floor) : 1.f;
-        const float km1 = v1 ? fmaf(d.kap[off + j1], c.invM, p.ru_floor) : 1.f;
-        const float rh0 = v0 ? d.rh[off + j0] : 0.f, rh1 = v1 ? d.rh[off + j1] : 0.f;
-        const float ru0 = v0 ? d.ru[off + j0] : 1.f, ru1 = v1 ? d.ru[off + j1] : 1.f;
-        if (ckpt) {                                      // the state entering this pass
-            float* crh = d.ckpt_rh + kc * d.n_slots + off;
-            float* cru = d.ckpt_ru + kc * d.n_slots + off;
-            if (v0) { crh[j0] = rh0; cru[j0] = ru0; }
-            if (v1) { crh[j1] = rh1; cru[j1] = ru1; }
-        }
-        f32x2 rh = pk(rh0, rh1), ru = pk(ru0, ru1), B;
-        const f32x2 cb = q == np - 1 ? pk(v0 ? p.c_b : 0.f, v1 ? p.c_b : 0.f) : k.CB;
-        pass_a_pair(k, pk(t0.x, t1.x), pk(t0.y, t1.y), pk(t0.z, t1.z), pk(t0.w, t1.w), pk(km0, km1), cb, rh, ru, B,
-                    part);
-        if (v0) d.rh[off + j0] = lo_of(rh);
-        if (v1) d.rh[off + j1] = hi_of(rh);
-        s_am[q][tid] = ru;
-        s_b[q][tid] = B;
-    }
-    if (ckpt && tid == 0) d.ckpt_lam[kc * d.n_rows + r] = lam0;
-    const float lam = block_sum<BLOCK>(lo_of(part) + hi_of(part), red, 0) * (1.0f / (float)J);
-    const f32x2 ILM = dup(rcp_refined(lam) * c.invM);
-    bool clamp = false;
-    for (int q = 0; q < np; ++q) {
-        const f32x2 ru = fma2(s_b[q][tid], ILM, s_am[q][tid]);
-        const int j0 = 2 * q * BLOCK + tid, j1 = j0 + BLOCK;
-        if (j0 < J) {
-            d.ru[off + j0] = lo_of(ru);
-            clamp |= lo_of(ru) <= p.ru_floor;
-        }
-        if (j1 < J) {
-            d.ru[off + j1] = hi_of(ru);
-            clamp |= hi_of(ru) <= p.ru_floor;
-        }
-    }
-    if (clamp) atomicOr(d.status, kFlagClamp);
-    if (tid == 0) {
-        d.lam[r] = lam;
-        if (!(lam > 0.f) || !(lam <= FLT_MAX)) atomicOr(d.status, kFlagNonfinite);
-    }
-}
+#include "stream_kernel.cuh"
 
 // Persistent variants: a fixed grid of resident CTAs takes rows from the order
 // table through an atomic counter (dynamic longest-first scheduling).
