@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--streaming-workload", default="scale-m8",
                     help="workload of the streaming section (its invariants + state must exceed L2)")
     ap.add_argument("--streaming-replicas", type=int, default=1)
+    ap.add_argument("--n-utt", type=int, default=None,
+                    help="use the first N utterances of a many-utterance workload (batch-256, adjoint-16)")
     ap.add_argument("--streaming-launches", type=int, default=50)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward + adjoint section")
     ap.add_argument("--adjoint-workload", default="adjoint-16")
@@ -194,9 +196,9 @@ def dist_env():
     return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def make_inputs(name):
+def make_inputs(name, n_utt=None):
     from paper_1908_01964_gb300 import synth
-    wl = synth.workload(name)
+    wl = synth.workload(name, n_utt=n_utt) if n_utt and name in ("batch-256", "adjoint-16") else synth.workload(name)
     workers = min(16, os.cpu_count() or 1) if len(wl.specs) > 8 else 1
     return wl, synth.make_workload(wl, workers=workers, inputs_only=True)
 
@@ -357,7 +359,7 @@ def run_ours(args):
     B.build()
     R.lib()
     dev = torch.device("cuda", torch.cuda.current_device())
-    wl, probs = make_inputs(args.workload)
+    wl, probs = make_inputs(args.workload, args.n_utt)
     n_iter = wl.n_iter
     slots = wl.slots
     dprobs = [R.to_device(p, dev) for p in probs]
@@ -548,7 +550,7 @@ def streaming_roofline(args, R, dev, peaks, stream, reuse=None):
     if reuse is not None:
         wl, dprobs = reuse
     else:
-        wl, probs = make_inputs(args.streaming_workload)
+        wl, probs = make_inputs(args.streaming_workload, args.n_utt)
         dprobs = [R.to_device(p, dev) for p in probs]
     copies = dprobs * args.streaming_replicas
     s = R.Solver(copies, rule="accel", iters_per_launch=1, block=args.block)

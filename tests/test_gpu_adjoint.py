@@ -26,11 +26,12 @@ def _prob(M, I, J, seed, lam_scale=1.3):
     return p
 
 
-def _gpu_grads(probs, K, stride, block=0, grad_from="gpu"):
+def _gpu_grads(probs, K, stride, block=0, iters_per_launch=0):
     """Forward + backward on the GPU; L = sum |h - h_true|^2 with g_h = 2 (h - h_true)."""
     from paper_1908_01964_gb300 import rcscm as R
     dev = [R.to_device(p) for p in probs]
-    with R.Solver(dev, ckpt_stride=stride, ckpt_max_iters=max(K, 1), block=block) as s:
+    with R.Solver(dev, ckpt_stride=stride, ckpt_max_iters=max(K, 1), block=block,
+                  iters_per_launch=iters_per_launch) as s:
         s.setup()
         s.iterate(K)
         h = s.extract()
@@ -95,6 +96,16 @@ def test_adjoint_is_independent_of_the_checkpoint_stride():
         got = _gpu_grads([p], K, stride=stride, block=128)
         for a, b in zip(ref[0], got[0]):
             assert np.array_equal(a, b), stride
+
+
+def test_checkpoints_from_the_streaming_kernel_give_the_same_gradients():
+    # one pass per launch runs the streaming kernel, which writes the checkpoints itself
+    p = _prob(4, I=4, J=700, seed=9)
+    K = 8
+    a = _gpu_grads([p], K, stride=3, block=256)
+    b = _gpu_grads([p], K, stride=3, block=256, iters_per_launch=1)
+    for x, y in zip(a[0], b[0]):
+        assert np.array_equal(x, y)
 
 
 @pytest.mark.parametrize("block", [128, 256])
