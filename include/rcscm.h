@@ -56,6 +56,10 @@ extern "C" {
 #define RCSCM_RULE_ACCEL  0  /* second-stage accelerated rule, Algorithm 2         */
 #define RCSCM_RULE_NAIVE  1  /* naive rule, Eqs. (eq:rijx)-(eq:M_ru), FP32 arithmetic */
 #define RCSCM_RULE_NAIVE_F64 2 /* naive rule in FP64 arithmetic (state kept in FP32)  */
+#define RCSCM_RULE_ACCEL1 3  /* first-stage accelerated rule, Algorithm 1: the per-slot
+                                quadratic forms with the per-frequency inverses are
+                                re-evaluated from x at every pass (O(M^2) per slot),
+                                rows of up to 4096 frames                             */
 
 #define RCSCM_MAX_M       8  /* largest supported number of microphones          */
 #define RCSCM_MAX_J_ACCEL 4096 /* longest row (frames) of the accelerated kernel  */
@@ -77,8 +81,8 @@ typedef struct {
 } rcscm_problem;
 
 typedef struct {
-    int    rule;             /* RCSCM_RULE_ACCEL (default), RCSCM_RULE_NAIVE or
-                                RCSCM_RULE_NAIVE_F64                                    */
+    int    rule;             /* RCSCM_RULE_ACCEL (default), RCSCM_RULE_NAIVE,
+                                RCSCM_RULE_NAIVE_F64 or RCSCM_RULE_ACCEL1               */
     double alpha;            /* inverse-gamma shape, Table II: 1.1                      */
     double beta;             /* inverse-gamma scale, Table II: 1e-16                    */
     float  ru_floor;         /* lower bound applied to r^(u) (default FLT_MIN)          */
@@ -133,7 +137,10 @@ int rcscm_setup(rcscm_ctx* ctx, void* stream);
  * (eq:1st_ru with the new lambda_i).  Naive rule: E-step (eq:rijx)-(eq:E_hru)
  * with an explicit M x M inverse per slot, then M-step (eq:M_rh)-(eq:M_ru); in
  * FP32 its r_h estimate and b^H R^u b, non-negative in exact arithmetic, are held
- * at zero when rounding makes them negative (reported as RCSCM_ECLAMP). */
+ * at zero when rounding makes them negative (reported as RCSCM_ECLAMP).
+ * First-stage rule: the repeat loop of Algorithm 1 (Sec. III-C-1), the same
+ * updates with rho~_ax and the r^(u) numerator re-evaluated from x_ij at every
+ * pass through the per-frequency inverses (Eq. (eq:riinv)). */
 int rcscm_iterate(rcscm_ctx* ctx, int n_iter, void* stream);
 
 /* Multichannel Wiener filter with the current state: the posterior mean

@@ -81,7 +81,9 @@ void free_all(rcscm_ctx* c) {
 }
 
 int valid_options(const rcscm_options* o) {
-    if (o->rule != RCSCM_RULE_ACCEL && o->rule != RCSCM_RULE_NAIVE && o->rule != RCSCM_RULE_NAIVE_F64) return 0;
+    if (o->rule != RCSCM_RULE_ACCEL && o->rule != RCSCM_RULE_NAIVE && o->rule != RCSCM_RULE_NAIVE_F64 &&
+        o->rule != RCSCM_RULE_ACCEL1)
+        return 0;
     if (!(o->alpha > -2.0) || !(o->beta >= 0.0)) return 0;
     if (!(o->null_tol > 0.0) || !(o->ru_floor >= 0.0f)) return 0;
     if (!accel_block_ok(o->block)) return 0;
@@ -155,6 +157,7 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
         if (!q.x || !q.a || !q.Rp || !q.rh0 || !q.ru0) return RCSCM_EINVAL;
         if (q.J > INT32_MAX / 2) return RCSCM_EINVAL;
         if (opt->rule == RCSCM_RULE_ACCEL && q.J > accel_max_j(opt->block)) return RCSCM_EINVAL;
+        if (opt->rule == RCSCM_RULE_ACCEL1 && accel1_block((int)q.J) == 0) return RCSCM_EINVAL;
         R += q.I;
         S += q.I * q.J;
         n_blocks += q.I * ((q.J + kSlotBlock - 1) / kSlotBlock);
@@ -343,6 +346,8 @@ int rcscm_iterate(rcscm_ctx* c, int n_iter, void* stream) {
         cudaError_t e;
         if (c->opt.rule == RCSCM_RULE_ACCEL)
             e = launch_accel(c->d, (int)c->R, c->max_j, c->opt.block, k, pk, c->opt.persistent != 0, cs);
+        else if (c->opt.rule == RCSCM_RULE_ACCEL1)
+            e = launch_accel1(c->d, (int)c->R, c->max_j, k, p, cs);
         else
             e = launch_naive(c->d, c->naive_rows, c->count_by_m, c->first_by_m, k, p,
                              c->opt.rule == RCSCM_RULE_NAIVE_F64, cs);

@@ -4,8 +4,10 @@
 
 // Streaming form of a launch that runs exactly one pass: the row's pairs are
 // loaded, updated and stored one at a time, with A/M and B of pass A kept in
-// shared memory for pass B, so few registers are live and several rows stream
-// through each SM.  Same operations in the same order and the same reduction as
+// shared memory for pass B, so few registers are live (at most 64, so that
+// 2048 threads of several rows stream through each SM).  Loading the next
+// pair ahead of the current one's arithmetic was measured to make no
+// difference.  Same operations in the same order and the same reduction as
 // the register-resident form, so the results are bitwise equal.
 // One pair of slots as loaded by the streaming kernel.
 struct PairIn {
@@ -47,14 +49,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) accel_stream_kernel(DevSt
     f32x2 part = dup(0.f);
     PairIn cur = load_pair(0);
     for (int q = 0; q < np; ++q) {
-#ifndef RCSCM_STREAM_PREFETCH
-#define RCSCM_STREAM_PREFETCH 1
-#endif
-#if RCSCM_STREAM_PREFETCH
-        const PairIn nxt = q + 1 < np ? load_pair(q + 1) : cur;    // in flight while pair q computes
-#else
         if (q > 0) cur = load_pair(q);
-#endif
         const int j0 = 2 * q * BLOCK + tid, j1 = j0 + BLOCK;
         const bool v0 = j0 < J, v1 = j1 < J;
         if (ckpt) {                                      // the state entering this pass
@@ -73,9 +68,6 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) accel_stream_kernel(DevSt
         if (v1) d.rh[off + j1] = hi_of(rh);
         s_am[q][tid] = ru;
         s_b[q][tid] = B;
-#if RCSCM_STREAM_PREFETCH
-        cur = nxt;
-#endif
     }
     if (ckpt && tid == 0) d.ckpt_lam[kc * d.n_rows + r] = lam0;
     const float lam = block_sum<BLOCK>(lo_of(part) + hi_of(part), red, 0) * (1.0f / (float)J);

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "librcscm.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "rcscm.h")
 
 OK, EINVAL, ENULLSPACE, ENONFINITE, ECLAMP, ECUDA, ENOMEM, ETIMEOUT, ECAPACITY = range(9)
-RULE_ACCEL, RULE_NAIVE, RULE_NAIVE_F64 = 0, 1, 2
+RULE_ACCEL, RULE_NAIVE, RULE_NAIVE_F64, RULE_ACCEL1 = 0, 1, 2, 3
 MAX_M = 8
 MAX_J_ACCEL = 4096
 FLT_MIN = float(np.finfo(np.float32).tiny)
@@ -118,7 +118,7 @@ def options(rule: str = "accel", alpha: float = 1.1, beta: float = 1e-16, ru_flo
             ckpt_stride: int = 0, ckpt_max_iters: int = 0) -> Options:
     o = Options()
     lib().rcscm_default_options(ctypes.byref(o))
-    o.rule = {"accel": RULE_ACCEL, "naive": RULE_NAIVE, "naive64": RULE_NAIVE_F64}[rule]
+    o.rule = {"accel": RULE_ACCEL, "naive": RULE_NAIVE, "naive64": RULE_NAIVE_F64, "accel1": RULE_ACCEL1}[rule]
     o.alpha, o.beta, o.ru_floor, o.null_tol = alpha, beta, ru_floor, null_tol
     o.block, o.iters_per_launch, o.persistent = block, iters_per_launch, int(persistent)
     o.ckpt_stride, o.ckpt_max_iters = int(ckpt_stride), int(ckpt_max_iters)

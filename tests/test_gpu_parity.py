@@ -393,3 +393,26 @@ def test_scale_m8_precision_at_1_10_200_passes():
     assert max(errs[1].values()) < TOL_ONE_ITER, errs
     assert max(errs[10].values()) < TOL_FULL_RUN and max(errs[200].values()) < TOL_FULL_RUN, errs
     assert errs["sdr_200"] > SDR_MIN_DB, errs
+
+
+# ------------------------------------------------------------------ first-stage rule (Algorithm 1)
+
+@pytest.mark.parametrize("M", [2, 3, 4, 6, 8])
+def test_first_stage_one_pass_and_full_run(M):
+    p = _tiny(M, I=9, J=300, seed=60 + M)
+    for n_iter, tol in ((1, TOL_ONE_ITER), (30, TOL_FULL_RUN)):
+        (g,), st = gpu_run([p], n_iter, rule="accel1")
+        e = compare(g, oracle_run(p, n_iter, rule="accel1"))
+        report("first_stage", M=M, n_iter=n_iter, gpu=e, status=st)
+        assert st == 0 and max(e["rh"], e["ru"], e["lam"]) < tol and e["sdr"] > SDR_MIN_DB, (n_iter, e)
+
+
+def test_first_stage_equals_second_stage_bitwise():
+    # Algorithm 1 and Algorithm 2 compute the same updates; at the same block size
+    # the kernels agree bit for bit
+    probs = [_tiny(M, I=4, J=J, seed=70 + M) for M, J in ((2, 100), (4, 1000), (6, 2048))]
+    a, _ = gpu_run(probs, 12, rule="accel1")
+    b, _ = gpu_run(probs, 12, rule="accel", block=256)
+    for x, y in zip(a, b):
+        for k in ("rh", "ru", "lam", "h"):
+            np.testing.assert_array_equal(x[k], y[k])
