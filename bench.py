@@ -533,7 +533,13 @@ def run_ours(args):
 
     # ---------------- end to end through the C ABI with host buffers
     if not args.no_e2e and len(probs) == 1 and args.replicas == 1:
-        result["e2e"] = e2e_host(probs[0], n_iter, args, R, n_chunks=args.e2e_chunks)
+        piped = e2e_host(probs[0], n_iter, args, R, n_chunks=args.e2e_chunks)
+        zc = e2e_zero_copy(probs[0], n_iter, args, R) if args.rule == "accel" else None
+        best = zc if zc is not None and zc["value"] > piped["value"] else piped
+        result["e2e"] = best
+        result["e2e_pipelined"] = piped
+        if zc is not None:
+            result["e2e_zero_copy"] = zc
         result["e2e_oneshot"] = e2e_oneshot(probs[0], n_iter, args, R)
     elif not args.no_e2e:
         result["e2e"] = None
@@ -661,6 +667,38 @@ def e2e_host(p, n_iter, args, R, n_chunks=4):
     return {"value": I * J * n_iter / t, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": h.numel() * h.element_size(), "ms_per_step": 1e3 * t, "steps": k,
             "api": f"rcscm_host_run (plan of {n_chunks} row chunks, page-locked host buffers, synchronous)"}
+
+
+def e2e_zero_copy(p, n_iter, args, R):
+    """rcscm_solve on buffers in page-locked host memory: the kernels read x, a,
+    R', r_h0, r_u0 and write h in place over the host link (no staging copies);
+    the step ends when h is complete in host memory."""
+    import torch
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    hp = dict(x=pin(p["x"].astype(np.complex64)), a=pin(p["a"].astype(np.complex128)),
+              Rp=pin(p["Rp"].astype(np.complex128)), rh0=pin(p["rh0"].astype(np.float32)),
+              ru0=pin(p["ru0"].astype(np.float32)))
+    I, J, M = hp["x"].shape
+    with R.Solver([hp], rule=args.rule, block=args.block) as s:
+        h = torch.empty(s.out_elements, dtype=torch.complex64).pin_memory()
+        for _ in range(3):
+            s.solve(n_iter, out=h)
+        torch.cuda.synchronize()
+        k = max(3, min(args.steps, 50))
+        times = []
+        for _ in range(k):
+            t0 = time.perf_counter()
+            s.solve(n_iter, out=h)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        code = s.status()
+    t = statistics.median(times)
+    return {"value": I * J * n_iter / t, "unit": UNIT,
+            "h2d_bytes_per_step": sum(v.numel() * v.element_size() for v in hp.values()),
+            "d2h_bytes_per_step": h.numel() * h.element_size(), "ms_per_step": 1e3 * t, "steps": k,
+            "status": R.strerror(code),
+            "api": "rcscm_solve with every buffer in page-locked host memory, read and written in place "
+                   "by the kernels over the host link (no staging copies); synchronous per step"}
 
 
 def e2e_oneshot(p, n_iter, args, R):

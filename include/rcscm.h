@@ -66,9 +66,13 @@ extern "C" {
 
 typedef struct rcscm_ctx rcscm_ctx;
 
-/* One utterance.  All pointers are device pointers and must stay valid (and
- * unchanged) from rcscm_create until rcscm_destroy; rcscm_setup reads x, a, Rp,
- * lambda0, rh0, ru0, and the naive rule re-reads x at every iteration. */
+/* One utterance.  The pointers are device pointers of the current device or
+ * page-locked host memory (cudaHostAlloc / cudaHostRegister), which the kernels
+ * then read in place over the host link; any other address (pageable host
+ * memory, another device) makes rcscm_create return EINVAL.  They must stay
+ * valid (and unchanged) from rcscm_create until rcscm_destroy; rcscm_setup reads
+ * x, a, Rp, lambda0, rh0, ru0, rcscm_run reads x, rh0, ru0, and the naive and
+ * first-stage rules re-read x at every iteration. */
 typedef struct {
     int64_t I, J, M;
     const void*   x;        /* complex64  [I][J][M]  observed STFT x_ij                 */
@@ -145,7 +149,8 @@ int rcscm_iterate(rcscm_ctx* ctx, int n_iter, void* stream);
 
 /* Multichannel Wiener filter with the current state: the posterior mean
  * h_ij = r^(h) a a^H (R^(x)_ij)^{-1} x_ij = [r^(h) rho^(ax) / (r^(u) + r^(h) rho^(aa))] a_i.
- * h_out: device complex64, the utterances concatenated in order, each [I][J][M]. */
+ * h_out: complex64, the utterances concatenated in order, each [I][J][M]; device
+ * memory or page-locked host memory (written in place), else EINVAL. */
 int rcscm_extract(rcscm_ctx* ctx, void* h_out, void* stream);
 
 /* The same work as rcscm_setup + rcscm_iterate(n_iter) + rcscm_extract(h_out),

@@ -108,6 +108,34 @@ IterParams iter_params(const rcscm_options& o) {
     return p;
 }
 
+// The address under which the current device reaches caller memory `p`: device or
+// managed memory of this device as is; page-locked host memory through its device
+// view (with the coherent host link of this platform kernels read and write it
+// directly).  Anything else -- pageable host memory, another device's memory, an
+// invalid address -- is refused (nothing is launched on it).
+template <class T>
+int device_view(T* p, T** out) {
+    *out = nullptr;
+    if (!p) return RCSCM_EINVAL;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, (const void*)p) != cudaSuccess) {
+        cudaGetLastError();
+        return RCSCM_EINVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RCSCM_ECUDA;
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+        if (at.type == cudaMemoryTypeDevice && at.device != dev) return RCSCM_EINVAL;
+        *out = p;
+        return RCSCM_OK;
+    }
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+        *out = static_cast<T*>(at.devicePointer);
+        return RCSCM_OK;
+    }
+    return RCSCM_EINVAL;
+}
+
 }  // namespace
 
 int* rcscm::ctx_status_word(rcscm_ctx* c) { return c ? c->d.status : nullptr; }
@@ -155,6 +183,12 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
         const rcscm_problem& q = probs[p];
         if (q.I < 1 || q.J < 1 || q.M < 2 || q.M > kMaxM) return RCSCM_EINVAL;
         if (!q.x || !q.a || !q.Rp || !q.rh0 || !q.ru0) return RCSCM_EINVAL;
+        const void* v;
+        const double* vd;
+        const float* vf;
+        if (device_view(q.x, &v) || device_view(q.a, &v) || device_view(q.Rp, &v) || device_view(q.rh0, &vf) ||
+            device_view(q.ru0, &vf) || (q.lambda0 && device_view(q.lambda0, &vd)))
+            return RCSCM_EINVAL;
         if (q.J > INT32_MAX / 2) return RCSCM_EINVAL;
         if (opt->rule == RCSCM_RULE_ACCEL && q.J > accel_max_j(opt->block)) return RCSCM_EINVAL;
         if (opt->rule == RCSCM_RULE_ACCEL1 && accel1_block((int)q.J) == 0) return RCSCM_EINVAL;
@@ -187,6 +221,13 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
     int64_t r = 0, s = 0, o = 0, sc = 0, b = 0, ao = 0, po = 0;
     for (int p = 0; p < n_probs; ++p) {
         const rcscm_problem& q = probs[p];
+        rcscm_problem qv = q;                  // the device views of the caller's buffers (checked above)
+        device_view(q.x, &qv.x);
+        device_view(q.a, &qv.a);
+        device_view(q.Rp, &qv.Rp);
+        device_view(q.rh0, &qv.rh0);
+        device_view(q.ru0, &qv.ru0);
+        if (q.lambda0) device_view(q.lambda0, &qv.lambda0);
         c->row0.push_back(r);
         c->slot0.push_back(s);
         c->out0.push_back(o);
@@ -197,12 +238,12 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
             rd.scratch_off = sc;
             rd.a_off = ao;
             rd.rp_off = po;
-            rd.x = static_cast<const float2*>(q.x) + i * q.J * q.M;
-            rd.a = static_cast<const double2*>(q.a) + i * q.M;
-            rd.Rp = static_cast<const double2*>(q.Rp) + i * q.M * q.M;
-            rd.lambda0 = q.lambda0 ? q.lambda0 + i : nullptr;
-            rd.rh0 = q.rh0 + i * q.J;
-            rd.ru0 = q.ru0 + i * q.J;
+            rd.x = static_cast<const float2*>(qv.x) + i * q.J * q.M;
+            rd.a = static_cast<const double2*>(qv.a) + i * q.M;
+            rd.Rp = static_cast<const double2*>(qv.Rp) + i * q.M * q.M;
+            rd.lambda0 = qv.lambda0 ? qv.lambda0 + i : nullptr;
+            rd.rh0 = qv.rh0 + i * q.J;
+            rd.ru0 = qv.ru0 + i * q.J;
             rd.J = (int)q.J;
             rd.M = (int)q.M;
             rd.prob = p;
@@ -370,10 +411,11 @@ static bool fused_config(const rcscm_options& o) {
 }
 
 int rcscm_run(rcscm_ctx* c, int n_iter, void* h_out, void* stream) {
-    if (!c || n_iter < 0 || !h_out || !fused_config(c->opt)) return RCSCM_EINVAL;
+    void* h = nullptr;
+    if (!c || n_iter < 0 || !fused_config(c->opt) || device_view(h_out, &h)) return RCSCM_EINVAL;
     const cudaError_t e = launch_accel(c->d, (int)c->R, c->max_j, c->opt.block, n_iter, iter_params(c->opt),
                                        c->opt.persistent != 0, static_cast<cudaStream_t>(stream),
-                                       static_cast<float2*>(h_out));
+                                       static_cast<float2*>(h));
     c->iters_done = n_iter;
     c->iter_block = c->opt.block;
     return map_cuda(e);
@@ -393,9 +435,9 @@ int rcscm_solve(rcscm_ctx* c, int n_iter, void* h_out, void* stream) {
 }
 
 int rcscm_extract(rcscm_ctx* c, void* h_out, void* stream) {
-    if (!c || !h_out) return RCSCM_EINVAL;
-    return map_cuda(launch_extract(c->d, c->n_blocks, static_cast<float2*>(h_out),
-                                   static_cast<cudaStream_t>(stream)));
+    void* h = nullptr;
+    if (!c || device_view(h_out, &h)) return RCSCM_EINVAL;
+    return map_cuda(launch_extract(c->d, c->n_blocks, static_cast<float2*>(h), static_cast<cudaStream_t>(stream)));
 }
 
 int rcscm_get_state(rcscm_ctx* c, int p, float* rh, float* ru, float* lambda, void* stream) {

@@ -132,9 +132,11 @@ def _stream(stream):
 
 
 def _dev(t, dtype, shape, name):
+    """Address of a CUDA tensor, or of a page-locked CPU tensor (which the library
+    reads or writes in place; it refuses any other host memory)."""
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError(f"{name} must be a CUDA tensor")
+    if not isinstance(t, torch.Tensor) or not (t.is_cuda or t.is_pinned()):
+        raise TypeError(f"{name} must be a CUDA tensor or a page-locked CPU tensor")
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if tuple(t.shape) != tuple(shape):
@@ -171,7 +173,8 @@ class Solver:
             q.lambda0 = _dev(lam0, torch.float64, (I,), "lambda0") if lam0 is not None else None
             self._keep.append(p)
             self.shapes.append((I, J, M))
-        self.device = problems[0]["x"].device
+        dev0 = problems[0]["x"].device
+        self.device = dev0 if dev0.type == "cuda" else torch.device("cuda", torch.cuda.current_device())
         self.opt = options(rule=rule, **opts)
         self.rule = rule
         ctx = c_void_p()
@@ -224,6 +227,8 @@ class Solver:
             return torch.empty(self.out_elements, dtype=torch.complex64, device=self.device)
         if out.dtype != torch.complex64 or out.numel() != self.out_elements or not out.is_contiguous():
             raise ValueError("out must be a contiguous complex64 tensor with one element per output")
+        if not (out.is_cuda or out.is_pinned()):
+            raise TypeError("out must be a CUDA tensor or a page-locked CPU tensor")
         return out
 
     def setup_freq(self, stream=None):
