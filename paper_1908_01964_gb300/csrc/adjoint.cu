@@ -70,6 +70,7 @@ constexpr int kStage = 2 * kMaxM + 5;                     // x (2M) + g_tau (2) 
 
 template <int BLOCK, int SPT>
 struct AdjShared {
+    float ga_w[2 * kMaxM];   // gradient of a from the Wiener filter (block-uniform)
     float red[2][BLOCK / 32];
     float redn[2][BLOCK / 32][8];
     float2 s_a[kMaxM], s_b[kMaxM], s_Pa[kMaxM], s_P[kMaxM * kMaxM];
@@ -145,7 +146,6 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     float p_taa = 0.f, p_taaM = 0.f, p_invtaa = 0.f, p_sab2 = 0.f, p_sre = 0.f, p_sim = 0.f;
     // uniform row adjoints (every thread holds the same value)
     float u_taa = 0.f, u_sab2 = 0.f, u_sre = 0.f, u_sim = 0.f;
-    float ga_w[2 * kMaxM];
     float g_lam = 0.f;
 
     // ---- 1. Wiener filter at the final state --------------------------------------------
@@ -213,12 +213,14 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
         float gil = v0[1];
         u_sre += v0[2];
         u_sim += v0[3];
+        if (tid == 0) {                                             // block-uniform values
 #pragma unroll
-        for (int i = 0; i < 4; ++i) ga_w[i] = v0[4 + i];
+            for (int i = 0; i < 4; ++i) sh.ga_w[i] = v0[4 + i];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) ga_w[4 + i] = v1[i];
+            for (int i = 0; i < 8; ++i) sh.ga_w[4 + i] = v1[i];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) ga_w[12 + i] = v2[i];
+            for (int i = 0; i < 4; ++i) sh.ga_w[12 + i] = v2[i];
+        }
         u_taa += graa;                                              // raa = taa + sab2 / lam
         u_sab2 += graa * il;
         gil += graa * c.sab2;
@@ -441,7 +443,7 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
             pva = zadd(pva, zmul(dP[lane][n], dva[n]));
         }
         // g_a = g_a(Wiener) + P v_a + 2 g_taa P a + b conj(g_sab)
-        double2 ga = make_double2((double)ga_w[2 * lane], (double)ga_w[2 * lane + 1]);
+        double2 ga = make_double2((double)sh.ga_w[2 * lane], (double)sh.ga_w[2 * lane + 1]);
         ga = zadd(ga, pva);
         ga = zadd(ga, zscale(pa, 2.0 * g_taa));
         ga = zadd(ga, zmul(dE[lane][0], zconj(g_sab)));

@@ -41,6 +41,7 @@ struct rcscm_ctx {
     float* seg_rh = nullptr;         // adjoint scratch: [stride][S], [stride][S], [stride][R]
     float* seg_ru = nullptr;
     float* seg_lam = nullptr;
+    int* ident = nullptr;            // rows 0..R-1 in order (row ranges of the fused kernel)
     int iters_done = 0;              // passes since the last setup / set_state
     int iter_block = 0;              // block of those passes (-1: mixed)
 };
@@ -139,6 +140,28 @@ int device_view(T* p, T** out) {
 }  // namespace
 
 int* rcscm::ctx_status_word(rcscm_ctx* c) { return c ? c->d.status : nullptr; }
+
+static bool fused_config(const rcscm_options& o) {
+    return o.rule == RCSCM_RULE_ACCEL && o.iters_per_launch == 0 && o.ckpt_stride == 0;
+}
+
+bool rcscm::ctx_fused(const rcscm_ctx* c) { return c && fused_config(c->opt); }
+
+void rcscm::ctx_state(rcscm_ctx* c, float** rh, float** ru, float** lam) {
+    *rh = c->d.rh;
+    *ru = c->d.ru;
+    *lam = c->d.lam;
+}
+
+int rcscm::run_rows(rcscm_ctx* c, int first_row, int n_rows, int n_iter, float2* h, cudaStream_t s) {
+    if (!c || !fused_config(c->opt) || first_row < 0 || n_rows < 0 || first_row + (int64_t)n_rows > c->R)
+        return RCSCM_EINVAL;
+    DevState d = c->d;                       // the same kernel over a contiguous range of rows
+    d.order = c->ident + first_row;
+    // one CTA per row: ranges may run concurrently on several streams, and the
+    // persistent form's row counter is per context
+    return map_cuda(launch_accel(d, n_rows, c->max_j, c->opt.block, n_iter, iter_params(c->opt), false, s, h));
+}
 
 extern "C" {
 
@@ -308,6 +331,7 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
     if (!st) st = dalloc(c, &d.counter, 1);
     if (!st) st = dalloc(c, &d.obj_part, (size_t)n_blocks);
     if (!st) st = dalloc(c, &c->first_block, (size_t)n_probs + 1);
+    if (!st) st = dalloc(c, &c->ident, Rz);
     if (!st) st = dalloc(c, &c->obj_out, (size_t)n_probs);
     if (!st) {
         int dev = 0;
@@ -348,6 +372,9 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
     cudaError_t e = cudaMemcpyAsync(d.rows, rows.data(), Rz * sizeof(RowDesc), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.bmap, bmap.data(), (size_t)n_blocks * sizeof(BlockMap), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.order, order.data(), Rz * sizeof(int), cudaMemcpyHostToDevice, cs);
+    std::vector<int> ident((size_t)R);
+    std::iota(ident.begin(), ident.end(), 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ident, ident.data(), Rz * sizeof(int), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->naive_rows, naive_rows.data(), Rz * sizeof(int), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->first_block, first_block.data(), first_block.size() * sizeof(int),
@@ -404,10 +431,6 @@ int rcscm_iterate(rcscm_ctx* c, int n_iter, void* stream) {
 int rcscm_setup_freq(rcscm_ctx* c, void* stream) {
     if (!c) return RCSCM_EINVAL;
     return map_cuda(launch_setup(c->d, (int)c->R, c->opt.null_tol, static_cast<cudaStream_t>(stream)));
-}
-
-static bool fused_config(const rcscm_options& o) {
-    return o.rule == RCSCM_RULE_ACCEL && o.iters_per_launch == 0 && o.ckpt_stride == 0;
 }
 
 int rcscm_run(rcscm_ctx* c, int n_iter, void* h_out, void* stream) {

@@ -248,6 +248,15 @@ struct AdjointArgs {
 namespace rcscm {
 // Device status word of a context (api.cu), for the host pipeline's asynchronous status reads.
 int* ctx_status_word(rcscm_ctx* c);
+// The fused form (rcscm_run) on rows [first_row, first_row + n_rows) of a context in the
+// fused configuration, on `s` (api.cu; for the host pipeline).  h is the output of the
+// whole context: each row is written at its own offset in it.
+int run_rows(rcscm_ctx* c, int first_row, int n_rows, int n_iter, float2* h, cudaStream_t s);
+// Device state arrays of a context (r_h, r_u per slot, lambda per row; api.cu).
+void ctx_state(rcscm_ctx* c, float** rh, float** ru, float** lam);
+// True when rcscm_run applies to the context (accelerated rule, no checkpoints, all passes
+// in one launch).
+bool ctx_fused(const rcscm_ctx* c);
 cudaError_t launch_setup(const DevState& d, int n_rows, double null_tol, cudaStream_t s);
 cudaError_t launch_invariants(const DevState& d, int n_blocks, cudaStream_t s);
 // h != nullptr: the fused form (invariants from x, the passes, then the Wiener

@@ -324,17 +324,17 @@ def test_solve_host_matches_device_path():
         np.testing.assert_array_equal(r[k], g[k])
 
 
-@pytest.mark.parametrize("n_chunks", [1, 3])
-def test_host_plan_equals_device_path(n_chunks):
+@pytest.mark.parametrize("n_chunks,rule", [(1, "accel"), (3, "accel"), (8, "accel"), (4, "naive64")])
+def test_host_plan_equals_device_path(n_chunks, rule):
     """rcscm_host_run (chunked host pipeline) returns bit for bit what the
     device-resident context returns: rows are independent and every chunk uses
     the same kernel shape."""
     from paper_1908_01964_gb300 import rcscm as R
     p = _tiny(4, I=29, J=700, seed=14)
-    plan = R.HostPlan(*p["x"].shape, n_chunks=n_chunks)
+    plan = R.HostPlan(*p["x"].shape, n_chunks=n_chunks, rule=rule)
     for _ in range(2):                          # the plan is reusable
         r = plan.run(p, 9)
-        (g,), _ = gpu_run([p], 9)
+        (g,), _ = gpu_run([p], 9, rule=rule)
         for k in ("rh", "ru", "lam", "h"):
             np.testing.assert_array_equal(r[k], g[k])
     plan.close()
