@@ -125,3 +125,18 @@ def test_batch_subset_of_batch_256_sampled_rows():
         e = compare(g, oracle_run(p, wl.n_iter, rows=rows), rows=rows)
         assert max(e["rh"], e["ru"], e["lam"]) < TOL_FULL_RUN, e
         assert e["sdr"] > SDR_MIN_DB, e
+
+
+def test_sharded_batch_equals_unsharded():
+    # the shards two ranks would solve, run one after another on this GPU, give bit for
+    # bit the per-utterance results of the whole batch (same block size)
+    import bench
+    probs = _batch(n=7, seed=900, max_j=2048)
+    whole, _ = gpu_run(probs, 10, block=256)
+    weights = [p["x"].shape[0] * p["x"].shape[1] for p in probs]
+    for rank in range(2):
+        mine = bench.shard(weights, rank, 2)
+        part, _ = gpu_run([probs[i] for i in mine], 10, block=256)
+        for i, out in zip(mine, part):
+            for k in ("rh", "ru", "lam", "h"):
+                np.testing.assert_array_equal(out[k], whole[i][k])
