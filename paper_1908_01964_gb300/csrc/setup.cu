@@ -1,9 +1,9 @@
-// Per-frequency setup (FP64) and per-slot invariants (FP32) of the
+// Per-frequency setup (FP64 results) and per-slot invariants (FP32) of the
 // rank-constrained SCM estimator, sm_103a.
 //
 // setup_kernel   one group of 16 lanes per row (utterance, frequency i):
-//   R' <- (R' + R'^H)/2, Hermitian eigendecomposition (FP32 Jacobi sweeps, then
-//   FP64 iterative refinement of the eigenbasis),
+//   R' <- (R' + R'^H)/2, Hermitian eigendecomposition (parallel FP32 Jacobi
+//   sweeps, then iterative refinement of the eigenbasis to FP64 accuracy),
 //   b_i = eigenvector of the smallest eigenvalue (Sec. II-B-1), lambda_i = the
 //   next eigenvalue unless given (Sec. II-B-3), (R')^+ from the remaining pairs
 //   (Eq. (eq:riinv)), tau^(aa)_i (Eq. (eq:taa)), sigma^(ab)_i (Eq. (eq:sap)),
@@ -16,6 +16,14 @@
 //   kappa = tau^(xx) - |tau^(ax)|^2 / tau^(aa) >= 0 is formed as a sum of
 //   squares, without the cancellation of the difference.
 //
+//   The kernel is latency-bound on one row's chain of dependent operations, and
+//   on sm_103a every FP64 instruction (conversions included) holds the FP64 pipe
+//   of its SM sub-partition for tens of cycles per warp.  So FP64 is kept to the
+//   quantities whose accuracy needs it: the refinement's residuals and the
+//   FP64 outputs.  The Jacobi sweeps, the refinement's correction terms (of
+//   order |E|, where FP32 rounding adds 6e-8 |E|) and the FP32 per-row
+//   constants run on the FP32 pipe.
+//
 // invariants_kernel  one thread per slot: z = Phi_i x_ij, and initial state.
 #include <float.h>
 
@@ -24,135 +32,222 @@
 namespace rcscm {
 namespace {
 
-constexpr int kSetupWarps = 4;
+constexpr int kSetupWarps = 2;
 constexpr int kGroupLanes = 16;                             // lanes per row
 constexpr int kSetupRows = kSetupWarps * 32 / kGroupLanes;  // rows per block
 constexpr int kEntries = kMaxM * kMaxM / kGroupLanes;       // matrix entries per lane
 constexpr int kJacobiMaxSweeps32 = 12;
 constexpr int kRefineMaxSteps = 6;
 
-// Complex arithmetic for the FP32 Jacobi sweep.
-template <class R> struct Cplx;
-template <> struct Cplx<float> { using type = float2; };
-__device__ __forceinline__ float2 cx(float r, float i) { return make_float2(r, i); }
-template <class C> __device__ __forceinline__ C xadd(C a, C b) { return cx(a.x + b.x, a.y + b.y); }
-template <class C> __device__ __forceinline__ C xsub(C a, C b) { return cx(a.x - b.x, a.y - b.y); }
-template <class C, class R> __device__ __forceinline__ C xscale(C a, R s) { return cx(a.x * s, a.y * s); }
-template <class C> __device__ __forceinline__ C xmul(C a, C b) { return cx(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-template <class C> __device__ __forceinline__ C xmulc(C a, C b) { return cx(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
-template <class C> __device__ __forceinline__ auto xabs2(C a) { return a.x * a.x + a.y * a.y; }
-__device__ __forceinline__ float xrsqrt(float v) { return rsqrtf(v); }
+__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
-// Cyclic Jacobi sweeps on the Hermitian matrix A of this lane's group (lane k
-// owns index k), accumulating the rotations into V: A <- U^H A U, V <- V U.
-// With A_pq = m e^{i phi} and h = A_qq - A_pp, the rotation
-//   U = [[c, s], [-s e^{-i phi}, c e^{-i phi}]],  cos(2 theta) = |h| / sqrt(h^2 + 4 m^2),
-//   c = cos(theta), s = sign(h) sin(theta)   (|theta| <= pi/4)
-// zeroes A_pq; c and s come from three reciprocal square roots.  Only columns
-// p, q of A are updated and mirrored into rows p, q (A stays Hermitian); the
-// 2 x 2 diagonal block is set in closed form.  Sweeps stop when the
-// off-diagonal mass is at most tol2 * |A|_F^2 in every group of the warp.
-// Control flow containing __syncwarp is warp-uniform.
-template <class R>
-__device__ void jacobi_sweeps(typename Cplx<R>::type (*A)[kMaxM], typename Cplx<R>::type (*V)[kMaxM], int M,
-                              int Mw, int k, R tol2, R skip2, int max_sweeps) {
-    using C = typename Cplx<R>::type;
-    R fro2 = R(0);
-    for (int m = 0; m < M; ++m)
-        for (int n = 0; n < M; ++n) fro2 += xabs2(A[m][n]);
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        R off = R(0);
-        for (int p = 0; p < M; ++p)
-            for (int q = p + 1; q < M; ++q) off += xabs2(A[p][q]);
-        const bool conv = !(off > tol2 * fro2);
-        if (__all_sync(0xffffffffu, conv)) break;
-        for (int p = 0; p < Mw - 1; ++p) {
-            for (int q = p + 1; q < Mw; ++q) {
-                R c = R(1), s = R(0), app = R(0), aqq = R(0), m = R(0);
-                C ce = cx(R(1), R(0)), se = cx(R(0), R(0));     // c conj(e), s conj(e)
-                bool rot = false;
-                if (!conv && q < M) {
-                    const C apq = A[p][q];
-                    const R m2 = xabs2(apq);
-                    app = A[p][p].x;
-                    aqq = A[q][q].x;
-                    if (m2 > R(0) && m2 > skip2 * fabs(app * aqq)) {
-                        const R h = aqq - app;
-                        const R inv_m = xrsqrt(m2);
-                        m = m2 * inv_m;
-                        const R r = xrsqrt(fma(h, h, R(4) * m2));
-                        const R u = fma(R(0.5) * fabs(h), r, R(0.5));
-                        const R ru = xrsqrt(u);
-                        c = u * ru;
-                        s = copysign(m * r * ru, h);
-                        const C ec = cx(apq.x * inv_m, -apq.y * inv_m);   // conj(e)
-                        ce = xscale(ec, c);
-                        se = xscale(ec, s);
-                        rot = true;
-                    }
-                }
-                __syncwarp();
-                if (rot && k < M) {
-                    if (k != p && k != q) {        // columns p, q of A U, mirrored into rows p, q
-                        const C akp = A[k][p], akq = A[k][q];
-                        const C np = xsub(xscale(akp, c), xmul(se, akq));
-                        const C nq = xadd(xscale(akp, s), xmul(ce, akq));
-                        A[k][p] = np;
-                        A[k][q] = nq;
-                        A[p][k] = cx(np.x, -np.y);
-                        A[q][k] = cx(nq.x, -nq.y);
-                    } else if (k == p) {           // the 2 x 2 diagonal block
-                        const R cs2m = R(2) * c * s * m;
-                        A[p][p] = cx(fma(c * c, app, fma(s * s, aqq, -cs2m)), R(0));
-                        A[q][q] = cx(fma(s * s, app, fma(c * c, aqq, cs2m)), R(0));
-                        A[p][q] = cx(R(0), R(0));
-                        A[q][p] = cx(R(0), R(0));
-                    }
-                    const C vkp = V[k][p], vkq = V[k][q];   // V <- V U
-                    V[k][p] = xsub(xscale(vkp, c), xmul(se, vkq));
-                    V[k][q] = xadd(xscale(vkp, s), xmul(ce, vkq));
-                }
-                __syncwarp();
-            }
-        }
-    }
+// acc + a b, acc + conj(a) b and acc - conj(a) b, two fused multiply-adds per component
+// (every FP64 instruction counts on sm_103a).
+__device__ __forceinline__ double2 zfma(double2 acc, double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 zfma_c(double2 acc, double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 zfms_c(double2 acc, double2 a, double2 b) {
+    return make_double2(fma(-a.x, b.x, fma(-a.y, b.y, acc.x)), fma(-a.x, b.y, fma(a.y, b.x, acc.y)));
 }
 
 // Sum / maximum over the 16 lanes of a row group (xor offsets stay in the group).
-__device__ __forceinline__ double group_sum(double v) {
+__device__ __forceinline__ float group_sum_f(float v) {
 #pragma unroll
     for (int o = kGroupLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-__device__ __forceinline__ double group_max(double v) {
+__device__ __forceinline__ float group_max_f(float v) {
 #pragma unroll
-    for (int o = kGroupLanes / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = kGroupLanes / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
+// Integer key with the order of the doubles (negative values: low 63 bits flipped),
+// so that ranks are a permutation for any input, NaN included.
+__device__ __forceinline__ long long order_key(double v) {
+    const long long b = __double_as_longlong(v);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+
+// Partner of index x in round r (0 <= r < n - 1) of the circle schedule over n
+// indices (n even): index 0 keeps position 0, the others advance one position per
+// round, and the indices at positions k and n - 1 - k meet.  Over n - 1 rounds
+// every pair meets once.
+__device__ __forceinline__ int circle_partner(int x, int r, int n) {
+    const int n1 = n - 1;
+    int pos = x - 1 + r;
+    pos = pos >= n1 ? pos - n1 : pos;
+    pos = x == 0 ? 0 : pos + 1;
+    const int P = n1 - pos;
+    int v = P - 1 - r;
+    v = v < 0 ? v + n1 : v;
+    return P == 0 ? 0 : v + 1;
+}
+
+// Jacobi rotation of the pair (p, q), p < q, that zeroes A_pq.  With
+// A_pq = m e^{i phi} and h = A_qq - A_pp, U = [[c, s], [-s e^{-i phi}, c e^{-i phi}]]
+// on rows/columns (p, q), cos(2 theta) = |h| / sqrt(h^2 + 4 m^2), c = cos(theta),
+// s = sign(h) sin(theta) (|theta| <= pi/4); c and s come from three reciprocal
+// square roots.  The identity (on = false) when disabled, when p == q (an index
+// without a partner this round) or when A_pq is negligible.
+struct PairRot {
+    float c, s, m, app, aqq;
+    float2 ec;    // conj(e^{i phi})
+    bool on;
+};
+__device__ __forceinline__ PairRot pair_rot(const float2 (*A)[kMaxM], int p, int q, bool enable, float skip2) {
+    PairRot t;
+    t.app = A[p][p].x;
+    t.aqq = A[q][q].x;
+    const float2 apq = A[p][q];
+    const float m2 = cabs2(apq);
+    const float h = t.aqq - t.app;
+    const float inv_m = rsqrtf(m2);
+    const float r = rsqrtf(fmaf(h, h, 4.f * m2));
+    const float u = fmaf(0.5f * fabsf(h), r, 0.5f);
+    const float ru = rsqrtf(u);
+    // computed unconditionally (no branch between the two rotations of a round) and
+    // replaced by the identity where the rotation does not apply
+    t.on = enable && p != q && m2 > 0.f && m2 > skip2 * fabsf(t.app * t.aqq);
+    t.m = t.on ? m2 * inv_m : 0.f;
+    t.c = t.on ? u * ru : 1.f;
+    t.s = t.on ? copysignf(t.m * r * ru, h) : 0.f;
+    t.ec = t.on ? make_float2(apq.x * inv_m, -apq.y * inv_m) : make_float2(1.f, 0.f);
+    return t;
+}
+
+// Column k of a pair's U: (U_pk, U_qk) = (c, -s conj(e)) for k = p, (s, c conj(e)) for
+// k = q; (1, 0) for an index without a partner.
+__device__ __forceinline__ void rot_column(const PairRot& t, bool k_is_p, float& up, float2& uq) {
+    up = k_is_p ? t.c : t.s;
+    uq = k_is_p ? cscale(t.ec, -t.s) : cscale(t.ec, t.c);
+}
+
+// Parallel cyclic Jacobi in FP32 on the Hermitian matrix of this lane's group.
+// A sweep is n - 1 rounds of the circle schedule over n = M rounded up to even
+// indices; in a round the disjoint pairs rotate together, A <- U^H A U and
+// V <- V U, U the block-diagonal product of the pairs' rotations.  The warp runs
+// the rounds of its largest n; a group whose own rounds, or sweeps, are done
+// applies the identity (an exact copy), so each row's result does not depend on
+// the row that shares its warp.  Lanes own matrix entries and form the new ones from the previous
+// round's buffers (ping-pong), one warp synchronisation per round:
+//   new A_ij = conj(U_{p_i i}) (A_{p_i p_j} U_{p_j j} + A_{p_i q_j} U_{q_j j})
+//            + conj(U_{q_i i}) (A_{q_i p_j} U_{p_j j} + A_{q_i q_j} U_{q_j j})
+// for i < j in different pairs (mirrored into A_ji, so A stays exactly Hermitian),
+// A_pq = 0 and the closed-form 2 x 2 diagonal for the rotated pair's own entries.
+// Sweeps stop when the off-diagonal mass is at most tol2 |A|_F^2 in every group of
+// the warp.  Returns the buffer that holds the final A and V.  Control flow that
+// contains warp-wide synchronisation is uniform over the warp.
+__device__ int jacobi_parallel(float2 (*Ab0)[kMaxM], float2 (*Ab1)[kMaxM], float2 (*Vb0)[kMaxM],
+                               float2 (*Vb1)[kMaxM], int M, int l, float fro2, float tol2, float skip2,
+                               int max_sweeps) {
+    const int n = M + (M & 1);
+    const int nw = __reduce_max_sync(0xffffffffu, n);
+    const int MM = M * M;
+    int ei[kEntries], ej[kEntries];                       // this lane's entries (i, j)
+#pragma unroll
+    for (int t = 0; t < kEntries; ++t) {
+        const int e = l + kGroupLanes * t;
+        ei[t] = e < MM ? e / M : 0;
+        ej[t] = e < MM ? e - (e / M) * M : 0;
+    }
+    int cur = 0;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        const float2(*A)[kMaxM] = cur ? Ab1 : Ab0;
+        float off = 0.f;
+#pragma unroll
+        for (int t = 0; t < kEntries; ++t)
+            if (l + kGroupLanes * t < MM && ei[t] < ej[t]) off += cabs2(A[ei[t]][ej[t]]);
+        off = group_sum_f(off);
+        const bool conv = !(off > tol2 * fro2);
+        if (__all_sync(0xffffffffu, conv)) break;
+        for (int rd = 0; rd < nw - 1; ++rd) {
+            const bool rot = !conv && rd < n - 1;
+            const float2(*Ac)[kMaxM] = cur ? Ab1 : Ab0;
+            const float2(*Vc)[kMaxM] = cur ? Vb1 : Vb0;
+            float2(*An)[kMaxM] = cur ? Ab0 : Ab1;
+            float2(*Vn)[kMaxM] = cur ? Vb0 : Vb1;
+#pragma unroll
+            for (int t = 0; t < kEntries; ++t) {
+                if (l + kGroupLanes * t < MM) {
+                    const int i = ei[t], j = ej[t];
+                    // partners only within this group's own rounds (past them the schedule
+                    // formula leaves [0, n)); an index without a partner below M stays put
+                    int pi = circle_partner(i, rd, n);
+                    int pj = circle_partner(j, rd, n);
+                    pi = (rd < n - 1 && pi >= 0 && pi < M) ? pi : i;
+                    pj = (rd < n - 1 && pj >= 0 && pj < M) ? pj : j;
+                    const int ip = min(i, pi), iq = max(i, pi), jp = min(j, pj), jq = max(j, pj);
+                    // every operand first, then both rotations (independent chains)
+                    const float2 vp = Vc[i][jp], vq = Vc[i][jq];
+                    const float2 a00 = Ac[ip][jp], a01 = Ac[ip][jq], a10 = Ac[iq][jp], a11 = Ac[iq][jq];
+                    const PairRot rj = pair_rot(Ac, jp, jq, rot, skip2);
+                    const PairRot ri = pair_rot(Ac, ip, iq, rot, skip2);
+                    float bp, ap;
+                    float2 bq, aq;
+                    rot_column(rj, j == jp, bp, bq);
+                    rot_column(ri, i == ip, ap, aq);
+                    Vn[i][j] = cadd(cscale(vp, bp), cmul(vq, bq));
+                    if (i == j) {
+                        float2 v = (i == ip) ? a00 : a11;             // A_ii (unrotated)
+                        if (rj.on) {
+                            const float cs2m = 2.f * rj.c * rj.s * rj.m;
+                            v = (i == jp) ? make_float2(fmaf(rj.c * rj.c, rj.app, fmaf(rj.s * rj.s, rj.aqq, -cs2m)), 0.f)
+                                          : make_float2(fmaf(rj.s * rj.s, rj.app, fmaf(rj.c * rj.c, rj.aqq, cs2m)), 0.f);
+                        }
+                        An[i][i] = v;
+                    } else if (i < j) {
+                        float2 v = make_float2(0.f, 0.f);           // the rotated pair's own entry
+                        if (!(ip == jp && iq == jq && rj.on)) {
+                            const float2 rp = cadd(cscale(a00, bp), cmul(a01, bq));
+                            const float2 rq = cadd(cscale(a10, bp), cmul(a11, bq));
+                            v = cadd(cscale(rp, ap), cmulc(aq, rq));
+                        }
+                        An[i][j] = v;
+                        An[j][i] = cconj(v);
+                    }
+                }
+            }
+            __syncwarp();
+            cur ^= 1;
+        }
+    }
+    return cur;
+}
+
 // One row per group of 16 lanes (2 rows per warp).  The eigendecomposition of
-// R' runs in two phases.  Phase 1: cyclic Jacobi sweeps in FP32 (lane k owns
-// index k) give approximate eigenvectors X.  Phase 2, FP64: iterative
-// refinement of the whole eigenbasis (Ogita and Aishima's method, written
-// here for Hermitian matrices):
+// R' runs in two phases.  Phase 1: parallel Jacobi sweeps in FP32 give
+// approximate eigenvectors X.  Phase 2: iterative refinement of the whole
+// eigenbasis (Ogita and Aishima's method, written here for Hermitian matrices):
 //   R = I - X^H X,  S = X^H R' X,  lambda_i = S_ii / (1 - R_ii),
 //   E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)   (i != j, separated),
 //   E_ij = R_ij / 2                                         (diagonal, clusters),
 //   X <- X (I + E),
-// which converges quadratically and consists of matrix products only, so the
-// lanes of a group share its M x M entries (at most 4 each).  Control flow that
-// contains warp-wide synchronisation is uniform over the warp.
+// which converges quadratically.  R, S and lambda are the residuals and take
+// FP64; E and the product X E are corrections of order |E| and take FP32 (their
+// rounding, 6e-8 |E|, is below the next step's |E|^2 until |E| reaches 1e-7),
+// with X += X E accumulated in FP64.  1/(1 - R_ii) is the series
+// 1 + R_ii + R_ii^2, whose error R_ii^3 is below FP64 rounding because the
+// columns of X are unit vectors to FP32 accuracy (unitary rotations).  Lanes own
+// matrix entries (at most 4 each).  Control flow that contains warp-wide
+// synchronisation is uniform over the warp.
 __global__ void __launch_bounds__(kSetupWarps * 32)
 setup_kernel(DevState d, int n_rows, double null_tol) {
     __shared__ double2 sA[kSetupRows][kMaxM][kMaxM];    // R' (symmetrised)
     __shared__ double2 sX[kSetupRows][kMaxM][kMaxM];    // eigenvectors (columns)
-    __shared__ double2 sR[kSetupRows][kMaxM][kMaxM];    // I - X^H X   (phase 1: FP32 A and V)
-    __shared__ double2 sS[kSetupRows][kMaxM][kMaxM];    // X^H R' X
-    __shared__ double2 sT[kSetupRows][kMaxM][kMaxM];    // R' X, then E
+    __shared__ double2 sT[kSetupRows][kMaxM][kMaxM];    // R' X; later Householder data
+    __shared__ float2 sJ[kSetupRows][4][kMaxM][kMaxM];  // Jacobi A, V (two buffers each); later E
+    __shared__ float2 sX32[kSetupRows][kMaxM][kMaxM];   // FP32 copy of X for X E
+    __shared__ float2 sA32[kSetupRows][kMaxM][kMaxM];   // FP32 copy of R'
     __shared__ double slam[kSetupRows][kMaxM];
     __shared__ double2 sa[kSetupRows][kMaxM];
     __shared__ double2 sc[kSetupRows][kMaxM];
+    __shared__ double2 sf[kSetupRows][kMaxM];           // c_i / mu_i
     __shared__ double srs[kSetupRows][kMaxM];
+    __shared__ float2 sb32[kSetupRows][kMaxM];
     __shared__ int sperm[kSetupRows][kMaxM];
 
     const int g = threadIdx.x / kGroupLanes;
@@ -165,126 +260,138 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     const int MM = M * M;
     double2(*A)[kMaxM] = sA[g];
     double2(*X)[kMaxM] = sX[g];
-    double2(*Rm)[kMaxM] = sR[g];
-    double2(*S)[kMaxM] = sS[g];
     double2(*T)[kMaxM] = sT[g];
-    float2(*A32)[kMaxM] = reinterpret_cast<float2(*)[kMaxM]>(&sR[g][0][0]);
-    float2(*V32)[kMaxM] = reinterpret_cast<float2(*)[kMaxM]>(&sR[g][kMaxM / 2][0]);
+    float2(*X32)[kMaxM] = sX32[g];
+    float2(*E32)[kMaxM] = sJ[g][0];
 
-    double afro2 = 0.0;
+    float afro2 = 0.f;
     for (int e = l; e < MM; e += kGroupLanes) {
         const int m = e / M, n = e % M;
         const double2 amn = rd.Rp[m * M + n];
         const double2 anm = rd.Rp[n * M + m];
         const double2 h = make_double2(0.5 * (amn.x + anm.x), 0.5 * (amn.y - anm.y));
         A[m][n] = h;
-        afro2 += zabs2(h);
-        const float2 hf = make_float2((float)h.x, (float)h.y);
-        A32[m][n] = hf;
-        V32[m][n] = make_float2(m == n ? 1.f : 0.f, 0.f);
+        const float2 hf = to_f2(h);
+        afro2 += cabs2(hf);
+        sJ[g][0][m][n] = hf;
+        sA32[g][m][n] = hf;
+        sJ[g][2][m][n] = make_float2(m == n ? 1.f : 0.f, 0.f);
     }
     if (l < M) {
         const double2 av = rd.a[l];
         sa[g][l] = av;
-        d.a32[(size_t)r * kMaxM + l] = make_float2((float)av.x, (float)av.y);
+        d.a32[(size_t)r * kMaxM + l] = to_f2(av);
     }
-    const double afro = sqrt(group_sum(afro2));
+    afro2 = group_sum_f(afro2);
+    const float afro = sqrtf(afro2);
     __syncwarp();
-    const int Mw = __reduce_max_sync(0xffffffffu, M);
 
     // ---- phase 1: FP32 Jacobi sweeps ---------------------------------------------
-    jacobi_sweeps<float>(A32, V32, M, Mw, l, 1e-12f, 1e-14f, kJacobiMaxSweeps32);
+    const int jc = jacobi_parallel(sJ[g][0], sJ[g][1], sJ[g][2], sJ[g][3], M, l, afro2, 1e-12f, 1e-14f,
+                                   kJacobiMaxSweeps32);
     for (int e = l; e < MM; e += kGroupLanes) {
-        const float2 v = V32[e / M][e % M];
+        const float2 v = sJ[g][2 + jc][e / M][e % M];
         X[e / M][e % M] = make_double2(v.x, v.y);
+        X32[e / M][e % M] = v;
     }
     __syncwarp();
 
-    // ---- phase 2: FP64 refinement of the eigenbasis -------------------------------
-    for (int step = 0; step < kRefineMaxSteps; ++step) {
+    // ---- phase 2: refinement of the eigenbasis ------------------------------------
+    int ei[kEntries], ej[kEntries];                       // this lane's entries (i, j)
 #pragma unroll
-        for (int t = 0; t < kEntries; ++t) {                     // R = I - X^H X, T = R' X
+    for (int t = 0; t < kEntries; ++t) {
+        const int e = l + kGroupLanes * t;
+        ei[t] = e < MM ? e / M : 0;
+        ej[t] = e < MM ? e - (e / M) * M : 0;
+    }
+    bool done = false;                  // this group's refinement has converged
+    for (int step = 0; step < kRefineMaxSteps; ++step) {
+        double2 rv[kEntries], sv[kEntries];
+#pragma unroll
+        for (int t = 0; t < kEntries; ++t) {                     // R = I - X^H X, T = R' X (FP64)
             const int e = l + kGroupLanes * t;
             if (e < MM) {
-                const int i = e / M, j = e % M;
+                const int i = ei[t], j = ej[t];
                 double2 rr = make_double2(i == j ? 1.0 : 0.0, 0.0), tt = make_double2(0.0, 0.0);
                 for (int m = 0; m < M; ++m) {
-                    rr = zsub(rr, zmulc(X[m][i], X[m][j]));
-                    tt = zadd(tt, zmul(A[i][m], X[m][j]));
+                    rr = zfms_c(rr, X[m][i], X[m][j]);
+                    tt = zfma(tt, A[i][m], X[m][j]);
                 }
-                Rm[i][j] = rr;
+                rv[t] = rr;
                 T[i][j] = tt;
+                if (step > 0) X32[i][j] = to_f2(X[i][j]);
             }
         }
         __syncwarp();
-        double so2 = 0.0, rr2 = 0.0;
+        float so2 = 0.f, rr2 = 0.f;
 #pragma unroll
-        for (int t = 0; t < kEntries; ++t) {                     // S = X^H T
+        for (int t = 0; t < kEntries; ++t) {                     // S = X^H T (FP64), lambda
             const int e = l + kGroupLanes * t;
             if (e < MM) {
-                const int i = e / M, j = e % M;
+                const int i = ei[t], j = ej[t];
                 double2 ss = make_double2(0.0, 0.0);
-                for (int m = 0; m < M; ++m) ss = zadd(ss, zmulc(X[m][i], T[m][j]));
-                S[i][j] = ss;
-                if (i != j) so2 += zabs2(ss);
-                rr2 += zabs2(Rm[i][j]);
+                for (int m = 0; m < M; ++m) ss = zfma_c(ss, X[m][i], T[m][j]);
+                sv[t] = ss;
+                if (i == j) {
+                    const double rii = rv[t].x;
+                    if (!done) slam[g][i] = fma(ss.x, rii * (1.0 + rii), ss.x);
+                } else {
+                    so2 += cabs2(to_f2(ss));
+                }
+                rr2 += cabs2(to_f2(rv[t]));
             }
         }
-        const double delta = 2.0 * (sqrt(group_sum(so2)) + afro * sqrt(group_sum(rr2)));
+        so2 = group_sum_f(so2);
+        rr2 = group_sum_f(rr2);
+        const float delta = 2.f * (sqrtf(so2) + afro * sqrtf(rr2));
         __syncwarp();
-        if (l < M) slam[g][l] = S[l][l].x / (1.0 - Rm[l][l].x);
-        __syncwarp();
-        double emax = 0.0;
+        float emax = 0.f;
 #pragma unroll
-        for (int t = 0; t < kEntries; ++t) {                     // E (written over T)
+        for (int t = 0; t < kEntries; ++t) {                     // E (FP32)
             const int e = l + kGroupLanes * t;
             if (e < MM) {
-                const int i = e / M, j = e % M;
-                double2 ee;
+                const int i = ei[t], j = ej[t];
+                float2 ee;
                 if (i == j) {
-                    ee = make_double2(0.5 * Rm[i][j].x, 0.0);
+                    ee = make_float2(0.5f * (float)rv[t].x, 0.f);
                 } else {
-                    const double dl = slam[g][j] - slam[g][i];
-                    ee = fabs(dl) > delta ? zscale(zadd(S[i][j], zscale(Rm[i][j], slam[g][j])), 1.0 / dl)
-                                          : zscale(Rm[i][j], 0.5);
+                    const double lj = slam[g][j];
+                    const float dl = (float)(lj - slam[g][i]);
+                    ee = fabsf(dl) > delta ? cscale(to_f2(zadd(sv[t], zscale(rv[t], lj))), 1.f / dl)
+                                           : cscale(to_f2(rv[t]), 0.5f);
                 }
-                T[i][j] = ee;
-                emax = fmax(emax, zabs2(ee));
+                E32[i][j] = ee;
+                emax = fmaxf(emax, cabs2(ee));
             }
         }
-        emax = group_max(emax);
+        emax = group_max_f(emax);
         __syncwarp();
-        double2 nx[kEntries];
 #pragma unroll
         for (int t = 0; t < kEntries; ++t) {                     // X <- X + X E
             const int e = l + kGroupLanes * t;
-            if (e < MM) {
-                const int i = e / M, j = e % M;
-                double2 v = X[i][j];
-                for (int k = 0; k < M; ++k) v = zadd(v, zmul(X[i][k], T[k][j]));
-                nx[t] = v;
+            if (e < MM && !done) {
+                const int i = ei[t], j = ej[t];
+                float2 xe = make_float2(0.f, 0.f);
+                for (int k = 0; k < M; ++k) xe = cadd(xe, cmul(X32[i][k], E32[k][j]));
+                X[i][j] = zadd(X[i][j], make_double2(xe.x, xe.y));
             }
         }
         __syncwarp();
-#pragma unroll
-        for (int t = 0; t < kEntries; ++t) {
-            const int e = l + kGroupLanes * t;
-            if (e < MM) X[e / M][e % M] = nx[t];
-        }
-        __syncwarp();
-        // |E| <= 1e-6 was just applied: by quadratic convergence the remaining error is of
-        // order |E|^2 <= 1e-12 (scaled by the eigenvalue gaps): far below the FP32 outputs' rounding
-        // and the tolerances of the FP64 rule and the adjoint
-        if (__all_sync(0xffffffffu, !(emax > 1e-12))) break;
+        // |E| <= 1e-6 was just applied: the remaining error is of order |E|^2 <= 1e-12 (scaled by
+        // the eigenvalue gaps) plus the FP32 rounding of the correction, far below the FP32
+        // outputs' rounding and the tolerances of the FP64 rule and the adjoint.  A converged
+        // group leaves X and lambda alone while the other group of its warp continues.
+        done = done || !(emax > 1e-12f);
+        if (__all_sync(0xffffffffu, done)) break;
     }
 
     // ---- ascending order of the eigenvalues (ranks) --------------------------------
     if (l < M) {
-        const double li = slam[g][l];
+        const long long kl = order_key(slam[g][l]);
         int rank = 0;
         for (int j = 0; j < M; ++j) {
-            const double lj = slam[g][j];
-            rank += (lj < li) || (lj == li && j < l);
+            const long long kj = order_key(slam[g][j]);
+            rank += (kj < kl) || (kj == kl && j < l);
         }
         sperm[g][rank] = l;
     }
@@ -299,49 +406,59 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     if (l < M) {
         d.mu[(size_t)r * kMaxM + l] = slam[g][perm[l]];
         const double2 bv = X[l][k0];
+        const float2 bf = to_f2(bv);
         d.b64[(size_t)r * kMaxM + l] = bv;
-        d.b32[(size_t)r * kMaxM + l] = make_float2((float)bv.x, (float)bv.y);
+        d.b32[(size_t)r * kMaxM + l] = bf;
+        sb32[g][l] = bf;
     }
     if (d.evec64)                              // eigenbasis for the adjoint
         for (int e = l; e < MM; e += kGroupLanes) d.evec64[(size_t)r * 64 + e] = X[e / M][perm[e % M]];
-    // c_i = e_i^H a and 1/sqrt(mu_i) for the nonzero eigenpairs (sorted index i = 1..M-1)
+    // c_i = e_i^H a, 1/sqrt(mu_i) and c_i / mu_i for the nonzero eigenpairs (sorted index i = 1..M-1)
     if (l >= 1 && l < M) {
         const int kk = perm[l];
         double2 acc = make_double2(0.0, 0.0);
-        for (int m = 0; m < M; ++m) acc = zadd(acc, zmulc(X[m][kk], sa[g][m]));
+        for (int m = 0; m < M; ++m) acc = zfma_c(acc, X[m][kk], sa[g][m]);
+        const double rs = rsqrt(slam[g][kk]);
         sc[g][l] = acc;
-        srs[g][l] = rsqrt(slam[g][kk]);
+        srs[g][l] = rs;
+        sf[g][l] = zscale(acc, rs * rs);
     }
     __syncwarp(gmask);
 
-    double taa = 0.0;
-    for (int i = 1; i < M; ++i) taa += zabs2(sc[g][i]) * srs[g][i] * srs[g][i];
+    double taa = 0.0;                          // tau^(aa) = sum_i |c_i|^2 / mu_i
+    for (int i = 1; i < M; ++i) taa = fma(sc[g][i].x, sf[g][i].x, fma(sc[g][i].y, sf[g][i].y, taa));
     double2 sab = make_double2(0.0, 0.0);
-    for (int m = 0; m < M; ++m) sab = zadd(sab, zmulc(sa[g][m], X[m][k0]));
+    for (int m = 0; m < M; ++m) sab = zfma_c(sab, sa[g][m], X[m][k0]);
 
     const bool bad = !(mu2 > 0.0) || !(fabs(mu1) <= null_tol * muM) || !(taa > 0.0);
     if (l == 0 && bad) atomicOr(d.status, kFlagNullspace);
     const double lam0 = rd.lambda0 ? rd.lambda0[0] : mu2;
 
     // Householder vector for u = v / |v|, v_i = c_{i+1} / sqrt(mu_{i+1}), i = 0..M-2
-    const double nv = sqrt(taa);
-    const double inv_nv = nv > 0.0 ? 1.0 / nv : 0.0;
+    const double inv_nv = taa > 0.0 ? rsqrt(taa) : 0.0;
     const double2 u0 = zscale(sc[g][1], srs[g][1] * inv_nv);
-    const double au0 = sqrt(zabs2(u0));
-    const double2 ph0 = au0 > 0.0 ? zscale(u0, 1.0 / au0) : make_double2(1.0, 0.0);
-    // w = u - alpha e_0 with alpha = -ph0 |u| -> w_0 = ph0 (|u_0| + 1); |w|^2 = 2 + 2|u_0|
-    const double two_over_wn2 = 2.0 / (2.0 + 2.0 * au0);
+    const double au02 = zabs2(u0);
+    const double inv_au0 = au02 > 0.0 ? rsqrt(au02) : 0.0;
+    const double au0 = au02 * inv_au0;
+    const double2 ph0 = au02 > 0.0 ? zscale(u0, inv_au0) : make_double2(1.0, 0.0);
+    // w = u - alpha e_0 with alpha = -ph0 |u| -> w_0 = ph0 (|u_0| + 1); 2 / |w|^2 = 1 / (1 + |u_0|)
+    const double two_over_wn2 = 1.0 / (1.0 + au0);
 
     // Householder data shared by the rows of Phi (in the refinement's T array, free by
-    // now): w_i (i = 1..M-1) and q_n = sum_i conj(w_i e_i[n]) / sqrt(mu_i), once per n.
-    double2* wd = &sT[g][0][0];
-    double2* qd = &sT[g][1][0];
-    if (l >= 1 && l < M)   // w = u - alpha e_0 in the whitened basis, u_i = c_{i+1} / (sqrt(mu_{i+1}) |v|)
-        wd[l] = (l == 1) ? zscale(ph0, au0 + 1.0) : zscale(sc[g][l], inv_nv * srs[g][l]);
+    // now): w_i and conj(w_i) / sqrt(mu_i) (i = 1..M-1), then
+    // q_n = sum_i conj(w_i e_i[n]) / sqrt(mu_i), once per n.
+    double2* wd = &T[0][0];
+    double2* hq = &T[1][0];
+    double2* qd = &T[2][0];
+    if (l >= 1 && l < M) {   // w = u - alpha e_0 in the whitened basis, u_i = c_{i+1} / (sqrt(mu_{i+1}) |v|)
+        const double2 w = (l == 1) ? zscale(ph0, au0 + 1.0) : zscale(sc[g][l], inv_nv * srs[g][l]);
+        wd[l] = w;
+        hq[l] = zscale(zconj(w), srs[g][l]);
+    }
     __syncwarp(gmask);
     if (l < M) {
         double2 q = make_double2(0.0, 0.0);
-        for (int i = 1; i < M; ++i) q = zadd(q, zscale(zconj(zmul(wd[i], X[l][perm[i]])), srs[g][i]));
+        for (int i = 1; i < M; ++i) q = zfma_c(q, X[l][perm[i]], hq[i]);
         qd[l] = q;
     }
     __syncwarp(gmask);
@@ -350,10 +467,7 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     const float mu1f = (float)mu1;
     for (int e = l; e < MM; e += kGroupLanes) {
         const int m = e / M, n = e % M;
-        const float2 b_m = make_float2((float)X[m][k0].x, (float)X[m][k0].y);
-        const float2 b_n = make_float2((float)X[n][k0].x, (float)X[n][k0].y);
-        const float2 v = make_float2((float)A[m][n].x, (float)A[m][n].y);
-        d.rp32[(size_t)r * 64 + e] = csub(v, cscale(cmul(b_m, cconj(b_n)), mu1f));
+        d.rp32[(size_t)r * 64 + e] = csub(sA32[g][m][n], cscale(cmul(sb32[g][m], cconj(sb32[g][n])), mu1f));
     }
     // Phi entries (kk, n): row 0 (R'^+ a)^H, rows 1..M-2 H L^H, row M-1 b^H (FP64, rounded once)
     float2* phi = d.phi + (size_t)r * 64;
@@ -362,8 +476,7 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
         double2 val;
         if (kk == 0) {                                   // conj(g_n), g = R'^+ a = sum_i e_i c_i / mu_i
             double2 gv = make_double2(0.0, 0.0);
-            for (int i = 1; i < M; ++i)
-                gv = zadd(gv, zscale(zmul(X[n][perm[i]], sc[g][i]), srs[g][i] * srs[g][i]));
+            for (int i = 1; i < M; ++i) gv = zfma(gv, X[n][perm[i]], sf[g][i]);
             val = zconj(gv);
         } else if (kk == M - 1) {
             val = zconj(X[n][k0]);
@@ -371,27 +484,28 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
             val = zsub(zscale(zconj(X[n][perm[kk + 1]]), srs[g][kk + 1]),
                        zscale(zmul(wd[kk + 1], qd[n]), two_over_wn2));
         }
-        phi[e] = make_float2((float)val.x, (float)val.y);
+        phi[e] = to_f2(val);
     }
     if (l == 0) {
         d.lam0[r] = lam0;
         d.taa64[r] = taa;
         d.sab64[r] = sab;
-        RowConst c;
-        const double tsafe = taa > 0.0 ? taa : 1.0;
-        c.taa = (float)taa;
-        c.taaM = (float)(taa / M);
-        c.inv_taa = (float)(1.0 / tsafe);
-        c.sab2 = (float)zabs2(sab);
-        c.sab_re = (float)sab.x;
-        c.sab_im = (float)sab.y;
-        c.invM = (float)(1.0 / M);
+        RowConst c;                                      // FP32 per-row constants, formed in FP32
+        const float taaf = (float)taa;
+        const float2 sabf = to_f2(sab);
+        const float invM = 1.f / (float)M;
+        c.taa = taaf;
+        c.taaM = taaf * invM;
+        c.inv_taa = taa > 0.0 ? 1.f / taaf : 1.f;
+        c.sab2 = cabs2(sabf);
+        c.sab_re = sabf.x;
+        c.sab_im = sabf.y;
+        c.invM = invM;
         c.pad = 0.f;
         d.rc[r] = c;
         d.lam[r] = (float)lam0;
     }
 }
-
 
 __global__ void __launch_bounds__(kSlotBlock) invariants_kernel(DevState d) {
     __shared__ float2 sphi[kMaxM * kMaxM];

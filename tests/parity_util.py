@@ -21,6 +21,26 @@ def rel(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
+def kappa_fp32_bound(x, a, st, kappa):
+    """Forward error bound of kappa_ij = sum_k |Phi_k x_ij|^2 (k = 1..M-2) formed in FP32
+    from an FP32 copy of any orthonormal-complement basis Phi (Sec. III-C-2, the
+    invariants of Algorithm 2).  With unit roundoff u = 2^-24, rounding Phi once and
+    accumulating M fused products gives |dz_k| <= (M + 1) u sum_n |Phi_kn| |x_n|; by
+    Cauchy-Schwarz the whole error E = (sum_k |dz_k|^2)^(1/2) is at most
+    (M + 1) u |x| (sum_k |Phi_k|^2)^(1/2), and sum_k |Phi_k|^2 = tr(R'^+) - |R'^+ a|^2 / tau_aa
+    does not depend on the basis.  Then |kappa^ - kappa| <= 2 kappa^(1/2) E + E^2 + M u kappa.
+    Where x is almost parallel to a (the DC bin), this floor is far above 1e-5 tau_xx."""
+    x = np.asarray(x, np.complex128)
+    M = x.shape[-1]
+    u = 2.0 ** -24
+    P = st.Rp_pinv
+    ga = np.einsum("imn,in->im", P, np.asarray(a, np.complex128))
+    rows2 = np.real(np.trace(P, axis1=1, axis2=2)) - np.sum(np.abs(ga) ** 2, axis=1) / st.tau_aa
+    E = (M + 1) * u * np.linalg.norm(x, axis=-1) * np.sqrt(np.maximum(rows2, 0.0))[:, None]
+    k = np.maximum(kappa, 0.0)
+    return 2.0 * np.sqrt(k) * E + E ** 2 + M * u * k
+
+
 def sdr_db(est, ref):
     ref = np.asarray(ref, np.complex128).ravel()
     err = np.asarray(est, np.complex128).ravel() - ref

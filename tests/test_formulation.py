@@ -60,3 +60,34 @@ def test_kernel_algebra_terms_are_non_negative():
     inv = O.invariants(x, p["a"], st)
     kappa = inv.tau_xx - np.abs(inv.tau_ax) ** 2 / st.tau_aa[:, None]
     assert np.all(kappa >= -1e-12 * inv.tau_xx)           # Cauchy-Schwarz in the R'^+ inner product
+
+
+@pytest.mark.parametrize("M", [3, 4, 6, 8])
+def test_kappa_fp32_bound_holds_for_any_complement_basis(M):
+    # the tolerance of the invariants' kappa: an FP32 projection through an exact basis of
+    # the whitened complement of a, rounded once, stays within kappa_fp32_bound in any basis
+    from parity_util import kappa_fp32_bound
+    p = synth.make_problem(synth.ProblemSpec(M=M, I=11, J=300, K=4, spacing=0.03), 10 + M)
+    x = p["x"].astype(complex)
+    a = p["a"].astype(complex)
+    st = O.setup(p["a"], p["Rp"])
+    inv = O.invariants(x, a, st)
+    kappa = inv.tau_xx - np.abs(inv.tau_ax) ** 2 / st.tau_aa[:, None]
+    bound = kappa_fp32_bound(x, a, st, kappa)
+    rng = np.random.default_rng(M)
+    worst = 0.0
+    for i in range(x.shape[0]):
+        mu, E = np.linalg.eigh(st.Rp[i])
+        L = E[:, 1:] / np.sqrt(mu[1:])                       # R'^+ = L L^H
+        v = L.conj().T @ a[i]
+        Q, _ = np.linalg.qr(np.column_stack([v, rng.standard_normal((M - 1, M - 2))
+                                             + 1j * rng.standard_normal((M - 1, M - 2))]))
+        for basis in (Q[:, 1:], Q[:, 1:] @ np.linalg.qr(rng.standard_normal((M - 2, M - 2))
+                                                          + 1j * rng.standard_normal((M - 2, M - 2)))[0]):
+            P = (L @ basis).conj().T.astype(np.complex64)   # rows orthogonal to L^H a, FP32
+            z = x[i].astype(np.complex64) @ P.T
+            k32 = np.sum(z.real.astype(np.float32) ** 2 + z.imag.astype(np.float32) ** 2, axis=1, dtype=np.float32)
+            err = np.abs(k32.astype(float) - kappa[i])
+            assert np.all(err <= bound[i]), (i, np.max(err / bound[i]))
+            worst = max(worst, float(np.max(err / inv.tau_xx[i])))
+    assert worst > 1e-6                                       # the DC bin's floor is well above FP32 rounding
