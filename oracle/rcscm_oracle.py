@@ -33,7 +33,8 @@ Readings where the paper is silent (each also listed in the design notes):
     the final parameters.
   * The objective is the observed-data log posterior of the generative model of
     Sec. II-B-1 (constants dropped), which every EM pass must not decrease.
-Every function here has a pin in tests/test_oracle_pins.py.
+Every function here has a pin in tests/test_oracle_pins.py (ilrma_init: in
+tests/test_oracle_ilrma.py).
 """
 from __future__ import annotations
 
@@ -80,6 +81,45 @@ def setup(a, Rp, lambda0=None) -> Setup:
     tau_aa = np.real(np.einsum("im,imn,in->i", np.conj(a), Rp_pinv, a))
     sigma_ab = np.einsum("im,im->i", np.conj(a), b)
     return Setup(Rp=Rp, mu=mu, b=b, Rp_pinv=Rp_pinv, lam0=lam0, tau_aa=tau_aa, sigma_ab=sigma_ab)
+
+
+@dataclass
+class IlrmaInit:
+    a: np.ndarray         # a_i = column n_h of W_i^{-1}   [I, M]
+    Rp: np.ndarray        # Eq. (eq:rit)                   [I, M, M]
+    rh0: np.ndarray       # Eq. (eq:rhinit)                [I, J]
+    ru0: np.ndarray       # Eq. (eq:ruinit)                [I, J]
+
+
+def ilrma_init(x, W, T, V, n_h=0) -> IlrmaInit:
+    """Inputs of the estimator from the outputs of the ILRMA stage.
+
+    W_i = (w_{i,1} ... w_{i,M})^H is ILRMA's demixing matrix, so W_i = A_i^{-1}
+    and the target's steering vector is column n_h of W_i^{-1} (Sec. II-A;
+    Sec. II-B-1 names it a_i).  R'_i is the back-projection of the M-1 noise
+    outputs w_{i,n}^H x_ij, n != n_h, averaged over the frames (Eq. (eq:rit),
+    Sec. II-B-1).  The initial variances follow Sec. II-B-3: r_h from the
+    target's NMF bases T (t_{ik,n_h}, [I, K]) and activations V (v_{kj,n_h},
+    [K, J]) (Eq. (eq:rhinit)), and r_u = (1/M) y^H (R'_i)^+ y with y the
+    back-projected noise image W_i^{-1} (w_1^H x, ..., 0 at n_h, ..., w_M^H x)^T
+    (Eq. (eq:ruinit)).  lambda_i starts at the minimum nonzero eigenvalue of
+    R'_i, which setup() computes.
+    """
+    x = np.asarray(x, np.complex128)
+    W = np.asarray(W, np.complex128)
+    I, J, M = x.shape
+    Winv = np.linalg.inv(W)                                      # A_i = W_i^{-1}
+    a = Winv[:, :, n_h].copy()
+    y = np.einsum("inm,ijm->ijn", W, x)                          # y_ijn = w_{i,n}^H x_ij
+    keep = np.ones(M)
+    keep[n_h] = 0.0                                              # the target output is left out
+    P = np.abs(y) ** 2 * keep                                    # |w_{i,n}^H x_ij|^2, 0 at n_h
+    Rp = np.einsum("imn,ijn,ikn->imk", Winv, P, np.conj(Winv)) / J
+    rh0 = np.asarray(T, np.float64) @ np.asarray(V, np.float64)  # sum_k t_ik v_kj
+    yu = np.einsum("imn,ijn->ijm", Winv, y * keep)               # back-projected noise image
+    Rp_pinv = np.linalg.pinv(Rp, hermitian=True)
+    ru0 = np.real(np.einsum("ijm,imn,ijn->ij", np.conj(yu), Rp_pinv, yu)) / M
+    return IlrmaInit(a=a, Rp=Rp, rh0=rh0, ru0=ru0)
 
 
 @dataclass
