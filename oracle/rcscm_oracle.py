@@ -117,7 +117,12 @@ def ilrma_init(x, W, T, V, n_h=0) -> IlrmaInit:
     Rp = np.einsum("imn,ijn,ikn->imk", Winv, P, np.conj(Winv)) / J
     rh0 = np.asarray(T, np.float64) @ np.asarray(V, np.float64)  # sum_k t_ik v_kj
     yu = np.einsum("imn,ijn->ijm", Winv, y * keep)               # back-projected noise image
-    Rp_pinv = np.linalg.pinv(Rp, hermitian=True)
+    # (R'_i)^+ of the rank-(M-1) R'_i: its smallest eigenvalue is the zero one (the
+    # reading of setup()); a relative cutoff would keep a rounding-level eigenvalue
+    # and swamp the quadratic form with its inverse
+    mu, E = np.linalg.eigh(0.5 * (Rp + np.conj(np.transpose(Rp, (0, 2, 1)))))
+    En = E[:, :, 1:]
+    Rp_pinv = np.einsum("imk,ik,ink->imn", En, 1.0 / mu[:, 1:], np.conj(En))
     ru0 = np.real(np.einsum("ijm,imn,ijn->ij", np.conj(yu), Rp_pinv, yu)) / M
     return IlrmaInit(a=a, Rp=Rp, rh0=rh0, ru0=ru0)
 

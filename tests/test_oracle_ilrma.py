@@ -67,7 +67,7 @@ def test_ilrma_init_equals_loops_on_tiny_inputs(M, n_h):
                     for c in range(M):
                         Rp[r, c] += abs(yn) ** 2 * A[r, n] * np.conj(A[c, n]) / J
         np.testing.assert_allclose(got.Rp[i], Rp, rtol=1e-12, atol=1e-12)
-        Rp_pinv = np.linalg.pinv(Rp, hermitian=True)
+        Rp_pinv = np.linalg.pinv(Rp, hermitian=True, rcond=1e-10)      # rank M-1: the zero eigenvalue dropped
         for j in range(J):
             rh = sum(T[i, k] * V[k, j] for k in range(K))
             assert abs(got.rh0[i, j] - rh) <= 1e-12 * rh
@@ -133,3 +133,17 @@ def test_back_projection_is_scale_invariant():
     np.testing.assert_allclose(got.Rp, ref.Rp, rtol=1e-10, atol=1e-12 * np.abs(ref.Rp).max())
     np.testing.assert_allclose(got.ru0, ref.ru0, rtol=1e-9)
     np.testing.assert_allclose(got.a * g[:, 1:2], ref.a, rtol=1e-10)
+
+
+def test_ruinit_at_full_size_rows_equals_the_closed_form():
+    # at some rows of the single-utterance workload (M = 4, I = 1025, J = 1000) the null
+    # eigenvalue of R' rounds to about 1.2e-15 of the largest (row 700), above a relative
+    # pseudo-inverse cutoff of M eps; (R')^+ must still drop it (R' has rank M-1)
+    from paper_1908_01964_gb300 import synth
+    p = synth.make_workload(synth.workload("single-m4"))[0]
+    rows = np.array([0, 1, 300, 699, 700, 701, 1024])
+    got = O.ilrma_init(p["x"][rows], p["W"][rows], p["T"][rows], p["V"], 0)
+    y = np.einsum("inm,ijm->ijn", p["W"][rows], p["x"][rows].astype(complex))
+    d = np.mean(np.abs(y) ** 2, axis=1)
+    cf = (np.abs(y[:, :, 1:]) ** 2 / d[:, None, 1:]).sum(axis=2) / 4
+    np.testing.assert_allclose(got.ru0, cf, rtol=1e-8)
