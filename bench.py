@@ -80,6 +80,8 @@ def parse():
                     help="use the first N utterances of a many-utterance workload (batch-256, adjoint-16)")
     ap.add_argument("--streaming-launches", type=int, default=50)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward + adjoint section")
+    ap.add_argument("--no-ilrma", action="store_true",
+                    help="skip the section that times the initialisation from ILRMA outputs")
     ap.add_argument("--adjoint-workload", default="adjoint-16")
     ap.add_argument("--adjoint-steps", type=int, default=5)
     return ap.parse_args()
@@ -167,6 +169,7 @@ KERNEL_SOURCES = {
     "setup_kernel": ["setup.cu", "rcscm_internal.cuh"],
     "naive_kernel": ["naive.cu", "rcscm_internal.cuh"],
     "adjoint_kernel": ["accel_common.cuh", "adjoint.cu", "rcscm_internal.cuh"],
+    "ilrma_init_kernel": ["ilrma.cu", "rcscm_internal.cuh"],
 }
 
 
@@ -560,6 +563,10 @@ def run_ours(args):
     if not args.no_adjoint and args.rule == "accel":
         result["adjoint"] = adjoint_section(args, R, dev, stream)
 
+    # ---------------- estimator inputs from the ILRMA stage's outputs (rcscm_ilrma_init)
+    if not args.no_ilrma and args.replicas == 1:
+        result["ilrma_init"] = ilrma_section(probs, R, dev, peaks, flush, stream, wl.name)
+
     # ---------------- end to end through the C ABI with host buffers
     if not args.no_e2e and len(probs) == 1 and args.replicas == 1:
         piped = e2e_host(probs[0], n_iter, args, R, n_chunks=args.e2e_chunks)
@@ -622,6 +629,48 @@ def streaming_roofline(args, R, dev, peaks, stream, reuse=None):
             "launch_us_median": 1e3 * t, "launches": n, "slot_updates_per_s": slots / (t / 1e3),
             "shape": {"block": shape[0], "persistent": shape[1], "autotuned": args.block == 0},
             "status": R.strerror(code)}
+
+
+def ilrma_section(probs, R, dev, peaks, flush, stream, case, reps=20):
+    """rcscm_ilrma_init on the workload's utterances (one launch each): a_i,
+    R'_i, r_h0, r_u0 from x, W, T, V (Sec. II-B-1, II-B-3).  HBM-bound: the
+    algorithmic bytes read x, W, T, V once and write a, R', r_h0, r_u0; L2 is
+    flushed before every timed call."""
+    import torch
+    utts = [R.ilrma_to_device(p, dev) for p in probs]
+    nbytes = 0
+    slots = 0
+    for u in utts:
+        I, J, M = u["x"].shape
+        K = u["T"].shape[1]
+        nbytes += I * J * M * 8 + I * M * M * 16 + I * K * 4 + K * J * 4     # x, W, T, V
+        nbytes += I * M * 16 + I * M * M * 16 + 2 * I * J * 4                 # a, R', r_h0, r_u0
+        slots += I * J
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        R.ilrma_init(utts, status=status, stream=stream)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        R.ilrma_init(utts, status=status, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    achieved = nbytes / (t / 1e3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic, tsrc = profiled_traffic("ilrma_init_kernel", case)
+    return {"ms": t, "launches": len(utts), "slots": slots, "slots_per_s": slots / (t / 1e3),
+            "status": int(status.item()),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "traffic_source": tsrc, "traffic_algorithmic": nbytes,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured burst copy)" if peaks
+                         else "fallback 6800 GB/s",
+                         "kernel": "ilrma_init_kernel<M> (one CTA per frequency row) + rhinit_kernel (T V); "
+                                   "L2 flushed before each call; traffic is both kernels' DRAM bytes"}}
 
 
 def adjoint_section(args, R, dev, stream):

@@ -291,6 +291,46 @@ int rcscm_solve_noalloc(int64_t I, int64_t J, int64_t M, const void* x, const vo
                         const rcscm_options* opt, int n_iter, float* rh, float* ru, float* lambda,
                         void* h_out, int* status, void* stream);
 
+/* Estimator inputs from the outputs of the ILRMA stage (Sec. II-A, Sec. II-B-1
+ * Eq. (eq:rit), Sec. II-B-3 Eqs. (eq:rhinit), (eq:ruinit)).  ILRMA gives per
+ * frequency i the demixing matrix W_i = (w_{i,1} ... w_{i,M})^H = A_i^{-1} and,
+ * for the target source n_h, the NMF bases t_{ik} and activations v_{kj}.  For
+ * each utterance this writes
+ *   a    complex128 [I][M]     column n_h of W_i^{-1} (the target's steering vector),
+ *   Rp   complex128 [I][M][M]  R'_i = (1/J) sum_j W_i^{-1} diag(|w_{i,n}^H x_ij|^2,
+ *                              with 0 at n = n_h) W_i^{-H}, Eq. (eq:rit),
+ *   rh0  float [I][J]          sum_k t_ik v_kj, Eq. (eq:rhinit),
+ *   ru0  float [I][J]          (1/M) y^H (R'_i)^+ y with the back-projected noise
+ *                              image y, Eq. (eq:ruinit), evaluated in its closed form
+ *                              (1/M) sum_{n != n_h} |w_{i,n}^H x_ij|^2 / d_n, d_n the
+ *                              mean power of output n,
+ * in the layouts of rcscm_problem, so the buffers can be passed to rcscm_create
+ * as they are (lambda_i then starts at the minimum nonzero eigenvalue of R'_i).
+ * W_i^{-1} and R'_i are formed in FP64, the frame sums from FP32 products with
+ * compensated accumulation.  Inputs and outputs are device memory or page-locked
+ * host memory of the calling process; the caller owns them.  The work of every
+ * utterance is enqueued on `stream` (one launch per utterance) without
+ * synchronising.  Returns RCSCM_EINVAL, before anything is launched, for a bad
+ * shape (M outside 2..RCSCM_MAX_M, K outside 1..256, n_h outside 0..M-1, I or J
+ * below 1) or pointer.  `status` (a device int, or NULL) receives the status bits
+ * of rcscm_status: RCSCM_ENULLSPACE's for a singular W_i or a noise output with
+ * zero power (R'_i would not have rank M-1), RCSCM_ENONFINITE's for a non-finite
+ * R'_i.  (The paper computes these inputs on the CPU before the iterations.) */
+typedef struct {
+    int64_t I, J, M, K;
+    int64_t n_h;           /* index of the target source, 0 <= n_h < M */
+    const void* x;         /* complex64 [I][J][M] observed STFT x_ij */
+    const void* W;         /* complex128 [I][M][M] demixing matrices, row n = w_{i,n}^H */
+    const float* T;        /* [I][K] NMF bases of the target source, t_{ik,n_h} */
+    const float* V;        /* [K][J] NMF activations of the target source, v_{kj,n_h} */
+    void* a;               /* out: complex128 [I][M] */
+    void* Rp;              /* out: complex128 [I][M][M] */
+    float* rh0;            /* out: [I][J] */
+    float* ru0;            /* out: [I][J] */
+} rcscm_ilrma;
+
+int rcscm_ilrma_init(const rcscm_ilrma* u, int n_utt, int* status, void* stream);
+
 /* Host-memory pipeline for utterances of one shape (I, J, M).  rcscm_host_create
  * allocates device buffers for one utterance and splits its frequency rows into
  * n_chunks contiguous ranges, each with its own context and stream (rows are

@@ -524,6 +524,47 @@ int rcscm_get_invariants(rcscm_ctx* c, int p, void* tau_ax, void* sigma_bx, floa
     return map_cuda(e);
 }
 
+int rcscm_ilrma_init(const rcscm_ilrma* u, int n_utt, int* status, void* stream) {
+    using namespace rcscm;
+    if (!u || n_utt < 1) return RCSCM_EINVAL;
+    int* st = nullptr;
+    if (status && device_view(status, &st)) return RCSCM_EINVAL;
+    std::vector<IlrmaArgs> args((size_t)n_utt);
+    for (int k = 0; k < n_utt; ++k) {               // validate every utterance before any launch
+        const rcscm_ilrma& q = u[k];
+        if (q.I < 1 || q.J < 1 || q.I > INT32_MAX || q.J > INT32_MAX || q.M < 2 || q.M > kMaxM || q.K < 1 ||
+            q.K > kIlrmaMaxK || q.n_h < 0 || q.n_h >= q.M)
+            return RCSCM_EINVAL;
+        IlrmaArgs& g = args[(size_t)k];
+        g.I = (int)q.I;
+        g.J = (int)q.J;
+        g.M = (int)q.M;
+        g.K = (int)q.K;
+        g.n_h = (int)q.n_h;
+        const void *x, *W;
+        const float *T, *V;
+        void *a, *Rp;
+        float *rh0, *ru0;
+        if (device_view(q.x, &x) || device_view(q.W, &W) || device_view(q.T, &T) || device_view(q.V, &V) ||
+            device_view(q.a, &a) || device_view(q.Rp, &Rp) || device_view(q.rh0, &rh0) || device_view(q.ru0, &ru0))
+            return RCSCM_EINVAL;
+        g.x = static_cast<const float2*>(x);
+        g.W = static_cast<const double2*>(W);
+        g.T = T;
+        g.V = V;
+        g.a = static_cast<double2*>(a);
+        g.Rp = static_cast<double2*>(Rp);
+        g.rh0 = rh0;
+        g.ru0 = ru0;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (const IlrmaArgs& g : args) {
+        const cudaError_t e = launch_ilrma_init(g, st, s);
+        if (e != cudaSuccess) return map_cuda(e);
+    }
+    return RCSCM_OK;
+}
+
 int rcscm_status(rcscm_ctx* c, int* flags, void* stream) {
     if (!c) return RCSCM_EINVAL;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);

@@ -40,6 +40,12 @@ class Options(ctypes.Structure):
                 ("ckpt_stride", c_int), ("ckpt_max_iters", c_int)]
 
 
+class Ilrma(ctypes.Structure):
+    _fields_ = [("I", c_int64), ("J", c_int64), ("M", c_int64), ("K", c_int64), ("n_h", c_int64),
+                ("x", c_void_p), ("W", c_void_p), ("T", c_void_p), ("V", c_void_p),
+                ("a", c_void_p), ("Rp", c_void_p), ("rh0", c_void_p), ("ru0", c_void_p)]
+
+
 class RcscmError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -94,6 +100,7 @@ def lib():
         "rcscm_host_create": (c_int, [POINTER(vp), c_int64, c_int64, c_int64, POINTER(Options), c_int]),
         "rcscm_host_run": (c_int, [vp, vp, vp, vp, vp, vp, vp, c_int, vp, vp, vp, vp]),
         "rcscm_host_destroy": (None, [vp]),
+        "rcscm_ilrma_init": (c_int, [POINTER(Ilrma), c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -361,6 +368,52 @@ class Solver:
         r, s, b = c_int64(), c_int64(), c_int64()
         _check(lib().rcscm_info(self.ctx, ctypes.byref(r), ctypes.byref(s), ctypes.byref(b)), "rcscm_info")
         return dict(rows=r.value, slots=s.value, device_bytes=b.value)
+
+
+def ilrma_init(utts, status=None, stream=None) -> list:
+    """Estimator inputs from the outputs of the ILRMA stage (rcscm_ilrma_init).
+
+    Each element of `utts` is a dict with x (complex64 [I, J, M]), W (complex128
+    [I, M, M], row n = w_{i,n}^H), T (float32 [I, K]), V (float32 [K, J]) as CUDA
+    or page-locked CPU tensors and n_h (int, default 0).  Returns one dict per
+    utterance with a (complex128 [I, M]), Rp (complex128 [I, M, M]), rh0 and ru0
+    (float32 [I, J]) as CUDA tensors on the inputs' device, in the layouts
+    Solver takes.  `status` (an int32 CUDA tensor of one element, or None)
+    receives the status bits.  Enqueued on `stream`; does not synchronise."""
+    import torch
+    arr = (Ilrma * len(utts))()
+    outs = []
+    for k, u in enumerate(utts):
+        I, J, M = u["x"].shape
+        K = u["T"].shape[1]
+        dev = u["x"].device if u["x"].is_cuda else torch.device("cuda", torch.cuda.current_device())
+        o = dict(a=torch.empty((I, M), dtype=torch.complex128, device=dev),
+                 Rp=torch.empty((I, M, M), dtype=torch.complex128, device=dev),
+                 rh0=torch.empty((I, J), dtype=torch.float32, device=dev),
+                 ru0=torch.empty((I, J), dtype=torch.float32, device=dev))
+        q = arr[k]
+        q.I, q.J, q.M, q.K, q.n_h = I, J, M, K, int(u.get("n_h", 0))
+        q.x = _dev(u["x"], torch.complex64, (I, J, M), "x")
+        q.W = _dev(u["W"], torch.complex128, (I, M, M), "W")
+        q.T = _dev(u["T"], torch.float32, (I, K), "T")
+        q.V = _dev(u["V"], torch.float32, (K, J), "V")
+        q.a, q.Rp, q.rh0, q.ru0 = (c_void_p(o[n].data_ptr()) for n in ("a", "Rp", "rh0", "ru0"))
+        outs.append(o)
+    st = None if status is None else _dev(status, torch.int32, (1,), "status")
+    _check(lib().rcscm_ilrma_init(arr, len(utts), st, _stream(stream)), "rcscm_ilrma_init")
+    return outs
+
+
+def ilrma_to_device(prob: dict, device="cuda") -> dict:
+    """The ILRMA-stage outputs of a generator problem (synth: x, W, T, V, n_h) as CUDA tensors."""
+    import torch
+    return dict(
+        x=torch.from_numpy(np.ascontiguousarray(prob["x"], np.complex64)).to(device),
+        W=torch.from_numpy(np.ascontiguousarray(prob["W"], np.complex128)).to(device),
+        T=torch.from_numpy(np.ascontiguousarray(prob["T"], np.float32)).to(device),
+        V=torch.from_numpy(np.ascontiguousarray(prob["V"], np.float32)).to(device),
+        n_h=int(prob.get("n_h", 0)),
+    )
 
 
 def to_device(prob: dict, device="cuda") -> dict:

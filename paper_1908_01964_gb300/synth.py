@@ -88,7 +88,9 @@ def make_problem(spec: ProblemSpec, seed: int) -> dict:
       rh0 float32    [I, J]      initial target variance
       ru0 float32    [I, J]      initial noise variance
     and the ground truth  a_true, h_true (complex64 [I, J, M], target image),
-    rh_true, ru_true, W (perturbed demixing matrices, complex128 [I, M, M]).
+    rh_true, ru_true; and the ILRMA stand-in's own outputs W (perturbed
+    demixing matrices, complex128 [I, M, M]), T (float32 [I, K]) and V
+    (float32 [K, J]) (the target's NMF factors with 1 % noise) and n_h = 0.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     M, I, J, K = spec.M, spec.I, spec.J, spec.K
@@ -156,6 +158,7 @@ def make_problem(spec: ProblemSpec, seed: int) -> dict:
         rh0=rh0.astype(np.float32), ru0=ru0.astype(np.float32),
         a_true=a_true, h_true=h_true.astype(np.complex64),
         rh_true=rh_true, ru_true=ru_true, W=W, spec=spec, seed=seed,
+        T=That.astype(np.float32), V=Vhat.astype(np.float32), n_h=0,
     )
 
 
@@ -203,7 +206,7 @@ def utterance_seed(wl: Workload, u: int) -> int:
     return int(np.random.SeedSequence([wl.seed, u]).generate_state(1, dtype=np.uint64)[0] >> 1)
 
 
-_INPUT_KEYS = ("x", "a", "Rp", "rh0", "ru0", "spec", "seed")
+_INPUT_KEYS = ("x", "a", "Rp", "rh0", "ru0", "spec", "seed", "W", "T", "V", "n_h")
 
 
 def _make_inputs_only(args):

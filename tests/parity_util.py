@@ -41,6 +41,36 @@ def kappa_fp32_bound(x, a, st, kappa):
     return 2.0 * np.sqrt(k) * E + E ** 2 + M * u * k
 
 
+def ilrma_fp32_bounds(x, W, n_h):
+    """Forward error bounds of the FP32 frame sums of the initialisation from the
+    ILRMA stage (Sec. II-B-1 Eq. (eq:rit), Sec. II-B-3 Eq. (eq:ruinit)).  With
+    unit roundoff u = 2^-24, y = W x formed from W rounded once and M fused
+    products has |dy_n| <= e_n = (M + 1) u sum_m |w_nm| |x_m|, so the output power
+    P_n = |y_n|^2 is off by at most dP_n = 2 |y_n| e_n + e_n^2; the frame mean d_n,
+    summed with compensation, by dd_n = mean_j dP_n + 4 u d_n.  Then
+    |R'^ - R'|_F <= sum_{n != n_h} dd_n |q_n|^2 (q_n the columns of W^{-1}) and
+    r_u0 = (1/M) sum_{n != n_h} P_n / d_n is off by at most
+    (1/M) sum_{n != n_h} (dP_n / d_n + P_n dd_n / d_n^2 + 3 u P_n / d_n).
+    Returns (bound on |dR'|_F per row [I], bound on |dr_u0| per slot [I, J])."""
+    u = 2.0 ** -24
+    x = np.asarray(x, np.complex128)
+    W = np.asarray(W, np.complex128)
+    M = x.shape[-1]
+    y = np.einsum("inm,ijm->ijn", W, x)
+    e = (M + 1) * u * np.einsum("inm,ijm->ijn", np.abs(W), np.abs(x))
+    P = np.abs(y) ** 2
+    dP = 2.0 * np.abs(y) * e + e ** 2
+    keep = np.ones(M)
+    keep[n_h] = 0.0
+    d = P.mean(axis=1)
+    dd = dP.mean(axis=1) + 4.0 * u * d
+    q2 = np.sum(np.abs(np.linalg.inv(W)) ** 2, axis=1)            # |q_n|^2, [I, M]
+    dR = np.sum(keep * dd * q2, axis=1)
+    ds = np.where(keep > 0, d, 1.0)[:, None, :]
+    dru = np.sum(keep * (dP / ds + P * dd[:, None, :] / ds ** 2 + 3.0 * u * P / ds), axis=2) / M
+    return dR, dru
+
+
 def sdr_db(est, ref):
     ref = np.asarray(ref, np.complex128).ravel()
     err = np.asarray(est, np.complex128).ravel() - ref

@@ -91,3 +91,24 @@ def test_kappa_fp32_bound_holds_for_any_complement_basis(M):
             assert np.all(err <= bound[i]), (i, np.max(err / bound[i]))
             worst = max(worst, float(np.max(err / inv.tau_xx[i])))
     assert worst > 1e-6                                       # the DC bin's floor is well above FP32 rounding
+
+
+@pytest.mark.parametrize("M,n_h", [(2, 0), (4, 0), (4, 3), (8, 5)])
+def test_ilrma_fp32_bounds_hold_for_an_fp32_evaluation(M, n_h):
+    # the tolerances of the GPU initialisation from ILRMA outputs: an FP32 evaluation
+    # of y = W x (W rounded once), powers and ratios stays within ilrma_fp32_bounds
+    from parity_util import ilrma_fp32_bounds
+    p = synth.make_problem(synth.ProblemSpec(M=M, I=9, J=300, K=6, spacing=0.03), 60 + M)
+    x, W = p["x"], p["W"]
+    ref = O.ilrma_init(x, W, p["T"], p["V"], n_h)
+    dR, dru = ilrma_fp32_bounds(x, W, n_h)
+    y = np.einsum("inm,ijm->ijn", W.astype(np.complex64), x.astype(np.complex64))
+    P = (y.real.astype(np.float32) ** 2 + y.imag.astype(np.float32) ** 2).astype(np.float64)
+    keep = np.ones(M)
+    keep[n_h] = 0.0
+    d = (P * keep).mean(axis=1)
+    Winv = np.linalg.inv(W)
+    Rp = np.einsum("imn,in,ikn->imk", Winv, d, np.conj(Winv))
+    ru = np.sum(keep * P / np.where(keep > 0, d, 1.0)[:, None, :], axis=2) / M
+    assert np.all(np.linalg.norm(Rp - ref.Rp, axis=(1, 2)) <= dR)
+    assert np.all(np.abs(ru - ref.ru0) <= dru)
