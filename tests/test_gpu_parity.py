@@ -342,6 +342,39 @@ def test_host_plan_equals_device_path(n_chunks, rule):
     plan.close()
 
 
+def test_host_plan_graph_follows_addresses_and_contents():
+    """The host pipeline replays a captured graph while the host addresses stay the
+    same: new contents in the same page-locked buffers give the new results, and
+    switching to other buffers captures again (bitwise equal to the device path)."""
+    import torch
+    from paper_1908_01964_gb300 import rcscm as R
+    probs = [_tiny(4, I=21, J=300, seed=s) for s in (61, 62)]
+    pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dt)).pin_memory()  # noqa: E731
+
+    def buffers(p):
+        return dict(x=pin(p["x"], np.complex64), a=pin(p["a"], np.complex128), Rp=pin(p["Rp"], np.complex128),
+                    rh0=pin(p["rh0"], np.float32), ru0=pin(p["ru0"], np.float32),
+                    h=torch.empty(p["x"].shape, dtype=torch.complex64).pin_memory())
+
+    def run(plan, b):
+        code = plan.run_ptrs(b["x"].data_ptr(), b["a"].data_ptr(), b["Rp"].data_ptr(), b["rh0"].data_ptr(),
+                             b["ru0"].data_ptr(), 7, b["h"].data_ptr())
+        assert code in (R.OK, R.ECLAMP), R.strerror(code)
+        return b["h"].numpy().copy()
+
+    want = [gpu_run([p], 7)[0][0]["h"] for p in probs]
+    plan = R.HostPlan(*probs[0]["x"].shape, n_chunks=3)
+    bufs = [buffers(p) for p in probs]
+    for k in (0, 1, 0, 1):                        # other addresses: capture again
+        np.testing.assert_array_equal(run(plan, bufs[k]), want[k])
+    for k in (1, 0):                              # same addresses (buffer set 0), new contents: replay
+        for name, dt in (("x", np.complex64), ("a", np.complex128), ("Rp", np.complex128), ("rh0", np.float32),
+                         ("ru0", np.float32)):
+            bufs[0][name].copy_(torch.from_numpy(np.ascontiguousarray(probs[k][name], dt)))
+        np.testing.assert_array_equal(run(plan, bufs[0]), want[k])
+    plan.close()
+
+
 # ------------------------------------------------------------------ full-size workload (sampled rows)
 
 def test_single_m4_full_size_sampled_rows():
