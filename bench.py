@@ -169,7 +169,7 @@ KERNEL_SOURCES = {
     "setup_kernel": ["setup.cu", "rcscm_internal.cuh"],
     "naive_kernel": ["naive.cu", "rcscm_internal.cuh"],
     "adjoint_kernel": ["accel_common.cuh", "adjoint.cu", "rcscm_internal.cuh"],
-    "ilrma_init_kernel": ["ilrma.cu", "rcscm_internal.cuh"],
+    "ilrma_init_kernel": ["ilrma.cu", "ilrma.cuh", "rcscm_internal.cuh"],
 }
 
 

@@ -11,6 +11,7 @@
 #include <numeric>
 #include <vector>
 
+#include "ilrma.cuh"
 #include "rcscm_internal.cuh"
 
 using namespace rcscm;

@@ -33,7 +33,7 @@
 // non-finite R'_i sets the non-finite bit.
 #include <float.h>
 
-#include "rcscm_internal.cuh"
+#include "ilrma.cuh"
 
 namespace rcscm {
 namespace {

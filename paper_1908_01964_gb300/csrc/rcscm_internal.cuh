@@ -274,21 +274,6 @@ cudaError_t launch_naive(const DevState& d, const int* rows_by_m, const int* cou
 cudaError_t launch_extract(const DevState& d, int n_blocks, float2* h_out, cudaStream_t s);
 // First-stage rule (accel1.cu): threads per row for rows of up to max_j frames (0: too long).
 int accel1_block(int max_j);
-// One utterance of rcscm_ilrma_init (device views of the caller's buffers).
-struct IlrmaArgs {
-    int I, J, M, K, n_h;
-    const float2* x;       // [I][J][M]
-    const double2* W;      // [I][M][M], row n = w_{i,n}^H
-    const float* T;        // [I][K]
-    const float* V;        // [K][J]
-    double2* a;            // [I][M]
-    double2* Rp;           // [I][M][M]
-    float* rh0;            // [I][J]
-    float* ru0;            // [I][J]
-};
-constexpr int kIlrmaMaxK = 256;   // NMF bases per source held in shared memory
-cudaError_t launch_ilrma_init(const IlrmaArgs& u, int* status, cudaStream_t s);
-
 cudaError_t launch_accel1(const DevState& d, int n_rows, int max_j, int n_iter, const IterParams& p,
                           cudaStream_t s);
 cudaError_t launch_adjoint(const DevState& d, int n_rows, int max_j, int block, const AdjointArgs& a,
