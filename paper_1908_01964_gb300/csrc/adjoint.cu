@@ -66,6 +66,17 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
     s = t;
 }
 
+// Unevaluated FP32 pairs hi + lo: the sum of two pairs with Knuth's error-free
+// TwoSum and Dekker's renormalisation (additions only, no contraction).
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float hi2, float lo2) {
+    const float s = hi + hi2;
+    const float bb = s - hi;
+    float e = (hi - (s - bb)) + (hi2 - bb);
+    e += lo + lo2;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
 constexpr int kStage = 2 * kMaxM + 5;                     // x (2M) + g_tau (2) + g_sigma (2) + g_txx
 
 template <int BLOCK, int SPT>
@@ -343,8 +354,8 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
                 g_rh[k] = grh;
                 g_ru[k] = gru;
             }
-            float rv[8] = {pr_rtaa, pr_slr, pr_sli, 0.f, 0.f, 0.f, 0.f, 0.f};
-            block_sum_n<BLOCK, 8>(rv, redn, (parity++) & 1);
+            float rv[3] = {pr_rtaa, pr_slr, pr_sli};
+            block_sum_n<BLOCK, 3>(rv, reinterpret_cast<float (*)[BLOCK / 32][3]>(redn), (parity++) & 1);
             u_taa += rv[0];
             u_sab2 += rv[0] * il;
             u_sre += rv[1] * il;
@@ -358,12 +369,17 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     // kappa = tau_xx - |tau_ax|^2 / tau_aa: its tau_ax part joins g_tau (where it largely
     // cancels the pass's own tau_ax gradient) and its tau_aa part joins p_taa.  Roles of
     // the summing threads: C = sum g_txx x x^H (M*M), v_a = sum x conj(g_tau) (M),
-    // v_b = sum x conj(g_sigma) (M), each accumulated in slot order with compensated
-    // (Kahan) FP32 sums: they cancel heavily in step 4, so plain FP32 accumulation would
-    // lose the result, and the compensated sum keeps it at the rounding of the terms
-    // without the cost of FP64 (on sm_103a FP64 runs at a small fraction of the FP32 rate).
+    // v_b = sum x conj(g_sigma) (M), with compensated (Kahan) FP32 sums: they cancel
+    // heavily in step 4, so plain FP32 accumulation would lose the result, and the
+    // compensated sum keeps it at the rounding of the terms without the cost of FP64 (on
+    // sm_103a FP64 runs at a small fraction of the FP32 rate).  Each role's slots are
+    // split over n_groups threads (contiguous slot ranges of every staged block); their
+    // partials are combined per role in group order as error-free FP32 pairs.
     float2 acc = make_float2(0.f, 0.f), comp = make_float2(0.f, 0.f);
     const int n_roles = MM + 2 * M;
+    const int n_groups = BLOCK / n_roles > 1 ? BLOCK / n_roles : 1;
+    const int role = tid % n_roles, grp = tid / n_roles;
+    const int span = (BLOCK + n_groups - 1) / n_groups;
     for (int k = 0; k < NK; ++k) {
         const int j = k * BLOCK + tid;
         float* my = stage + tid * kStage;
@@ -396,17 +412,18 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
             for (int i = 0; i < kStage; ++i) my[i] = 0.f;
         }
         __syncthreads();
-        if (tid < n_roles) {
-            for (int sl = 0; sl < BLOCK; ++sl) {
+        if (grp < n_groups) {
+            const int sl1 = min(BLOCK, (grp + 1) * span);
+            for (int sl = grp * span; sl < sl1; ++sl) {
                 const float* o = stage + sl * kStage;
                 float2 term;
-                if (tid < MM) {
-                    const int m = tid / M, n = tid % M;
+                if (role < MM) {
+                    const int m = role / M, n = role % M;
                     const float2 xm = make_float2(o[2 * m], o[2 * m + 1]), xn = make_float2(o[2 * n], o[2 * n + 1]);
                     term = cscale(cmul(xm, cconj(xn)), o[2 * kMaxM + 4]);
                 } else {
-                    const int m = (tid - MM) % M;
-                    const int q = tid < MM + M ? 0 : 2;                // g_tau or g_sigma
+                    const int m = (role - MM) % M;
+                    const int q = role < MM + M ? 0 : 2;               // g_tau or g_sigma
                     term = cmul(make_float2(o[2 * m], o[2 * m + 1]),
                                 make_float2(o[2 * kMaxM + q], -o[2 * kMaxM + q + 1]));
                 }
@@ -416,12 +433,22 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
         }
         __syncthreads();
     }
+    // the groups' partials of each role, combined in group order (stage is free again)
+    float4* part = reinterpret_cast<float4*>(stage);
+    if (grp < n_groups) part[grp * n_roles + role] = make_float4(acc.x, -comp.x, acc.y, -comp.y);
     // row-constant partials
     float pv[8] = {p_taa, p_taaM, p_invtaa, p_sab2, p_sre, p_sim, 0.f, 0.f};
-    block_sum_n<BLOCK, 8>(pv, redn, (parity++) & 1);
+    block_sum_n<BLOCK, 8>(pv, redn, (parity++) & 1);        // its barrier also publishes `part`
+    float4 tot = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid < n_roles)
+        for (int gi = 0; gi < n_groups; ++gi) {
+            const float4 q = part[gi * n_roles + tid];
+            pair_add(tot.x, tot.y, q.x, q.y);
+            pair_add(tot.z, tot.w, q.z, q.w);
+        }
 
     // ---- 4. setup adjoint in FP64 (warp 0) -----------------------------------------------
-    const double2 accd = make_double2((double)acc.x - (double)comp.x, (double)acc.y - (double)comp.y);
+    const double2 accd = make_double2((double)tot.x + (double)tot.y, (double)tot.z + (double)tot.w);
     if (tid < MM) dG[tid / M][tid % M] = accd;
     else if (tid < MM + M) dva[tid - MM] = accd;
     else if (tid < n_roles) dvb[tid - MM - M] = accd;
