@@ -23,6 +23,7 @@ struct rcscm_ctx {
     int64_t R = 0, S = 0;
     int n_blocks = 0;
     int max_j = 0;
+    int max_m = 0;
     DevState d;
     int* naive_rows = nullptr;
     int count_by_m[kMaxM + 1];
@@ -202,6 +203,7 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
     *out = nullptr;
     if (!probs || n_probs < 1 || !opt || !valid_options(opt)) return RCSCM_EINVAL;
     int64_t R = 0, S = 0, n_blocks = 0, naive_scratch = 0;
+    int max_m = 0;
     int max_j = 0;
     for (int p = 0; p < n_probs; ++p) {
         const rcscm_problem& q = probs[p];
@@ -221,6 +223,7 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
         n_blocks += q.I * ((q.J + kSlotBlock - 1) / kSlotBlock);
         naive_scratch += q.I * q.J * q.M * q.M;
         max_j = std::max<int>(max_j, (int)q.J);
+        max_m = std::max<int>(max_m, (int)q.M);
     }
     if (R > INT32_MAX || n_blocks > INT32_MAX) return RCSCM_EINVAL;
     rcscm_options eff = *opt;
@@ -237,6 +240,7 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
     c->S = S;
     c->n_blocks = (int)n_blocks;
     c->max_j = max_j;
+    c->max_m = max_m;
 
     // ---- host row tables ----------------------------------------------------
     std::vector<RowDesc> rows((size_t)R);
@@ -394,7 +398,7 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
 int rcscm_setup(rcscm_ctx* c, void* stream) {
     if (!c) return RCSCM_EINVAL;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_setup(c->d, (int)c->R, c->opt.null_tol, cs);
+    cudaError_t e = launch_setup(c->d, (int)c->R, c->max_m, c->opt.null_tol, cs);
     if (e == cudaSuccess) e = launch_invariants(c->d, c->n_blocks, cs);
     c->iters_done = 0;
     c->iter_block = 0;
@@ -431,7 +435,7 @@ int rcscm_iterate(rcscm_ctx* c, int n_iter, void* stream) {
 
 int rcscm_setup_freq(rcscm_ctx* c, void* stream) {
     if (!c) return RCSCM_EINVAL;
-    return map_cuda(launch_setup(c->d, (int)c->R, c->opt.null_tol, static_cast<cudaStream_t>(stream)));
+    return map_cuda(launch_setup(c->d, (int)c->R, c->max_m, c->opt.null_tol, static_cast<cudaStream_t>(stream)));
 }
 
 int rcscm_run(rcscm_ctx* c, int n_iter, void* h_out, void* stream) {

@@ -155,7 +155,7 @@ extern "C" int rcscm_solve_noalloc(int64_t I, int64_t J, int64_t M, const void* 
     p.c_a2_f64 = 1.0 / (opt->alpha + 2.0);
     p.c_b_f64 = opt->beta / (opt->alpha + 2.0);
     p.ckpt_first = 0;
-    if (e == cudaSuccess) e = launch_setup(d, (int)R, opt->null_tol, cs);
+    if (e == cudaSuccess) e = launch_setup(d, (int)R, (int)M, opt->null_tol, cs);
     if (e == cudaSuccess) e = launch_invariants(d, (int)(R * nbpr), cs);
     const int chunk = opt->iters_per_launch > 0 ? opt->iters_per_launch : (n_iter > 0 ? n_iter : 1);
     for (int done = 0; e == cudaSuccess && done < n_iter; done += chunk) {

@@ -257,7 +257,8 @@ void ctx_state(rcscm_ctx* c, float** rh, float** ru, float** lam);
 // True when rcscm_run applies to the context (accelerated rule, no checkpoints, all passes
 // in one launch).
 bool ctx_fused(const rcscm_ctx* c);
-cudaError_t launch_setup(const DevState& d, int n_rows, double null_tol, cudaStream_t s);
+// max_m: the largest M among the rows (selects the kernel shape).
+cudaError_t launch_setup(const DevState& d, int n_rows, int max_m, double null_tol, cudaStream_t s);
 cudaError_t launch_invariants(const DevState& d, int n_blocks, cudaStream_t s);
 // h != nullptr: the fused form (invariants from x, the passes, then the Wiener
 // output into h), for a state freshly set by the setup kernel.

@@ -35,7 +35,10 @@ namespace {
 constexpr int kSetupWarps = 2;
 constexpr int kGroupLanes = 16;                             // lanes per row
 constexpr int kSetupRows = kSetupWarps * 32 / kGroupLanes;  // rows per block
-constexpr int kEntries = kMaxM * kMaxM / kGroupLanes;       // matrix entries per lane
+// Matrix entries per lane: NE = 1 when every row of the launch has M <= 4 (the
+// kernel is instantiated for NE = 1 and NE = kMaxEntries, so the common small-M
+// launch carries neither the code nor the registers of the larger one).
+constexpr int kMaxEntries = kMaxM * kMaxM / kGroupLanes;
 constexpr int kJacobiMaxSweeps32 = 12;
 constexpr int kRefineMaxSteps = 6;
 
@@ -141,15 +144,16 @@ __device__ __forceinline__ void rot_column(const PairRot& t, bool k_is_p, float&
 // Sweeps stop when the off-diagonal mass is at most tol2 |A|_F^2 in every group of
 // the warp.  Returns the buffer that holds the final A and V.  Control flow that
 // contains warp-wide synchronisation is uniform over the warp.
+template <int NE>
 __device__ int jacobi_parallel(float2 (*Ab0)[kMaxM], float2 (*Ab1)[kMaxM], float2 (*Vb0)[kMaxM],
                                float2 (*Vb1)[kMaxM], int M, int l, float fro2, float tol2, float skip2,
                                int max_sweeps) {
     const int n = M + (M & 1);
     const int nw = __reduce_max_sync(0xffffffffu, n);
     const int MM = M * M;
-    int ei[kEntries], ej[kEntries];                       // this lane's entries (i, j)
+    int ei[NE], ej[NE];                       // this lane's entries (i, j)
 #pragma unroll
-    for (int t = 0; t < kEntries; ++t) {
+    for (int t = 0; t < NE; ++t) {
         const int e = l + kGroupLanes * t;
         ei[t] = e < MM ? e / M : 0;
         ej[t] = e < MM ? e - (e / M) * M : 0;
@@ -159,7 +163,7 @@ __device__ int jacobi_parallel(float2 (*Ab0)[kMaxM], float2 (*Ab1)[kMaxM], float
         const float2(*A)[kMaxM] = cur ? Ab1 : Ab0;
         float off = 0.f;
 #pragma unroll
-        for (int t = 0; t < kEntries; ++t)
+        for (int t = 0; t < NE; ++t)
             if (l + kGroupLanes * t < MM && ei[t] < ej[t]) off += cabs2(A[ei[t]][ej[t]]);
         off = group_sum_f(off);
         const bool conv = !(off > tol2 * fro2);
@@ -171,7 +175,7 @@ __device__ int jacobi_parallel(float2 (*Ab0)[kMaxM], float2 (*Ab1)[kMaxM], float
             float2(*An)[kMaxM] = cur ? Ab0 : Ab1;
             float2(*Vn)[kMaxM] = cur ? Vb0 : Vb1;
 #pragma unroll
-            for (int t = 0; t < kEntries; ++t) {
+            for (int t = 0; t < NE; ++t) {
                 if (l + kGroupLanes * t < MM) {
                     const int i = ei[t], j = ej[t];
                     // partners only within this group's own rounds (past them the schedule
@@ -234,6 +238,7 @@ __device__ int jacobi_parallel(float2 (*Ab0)[kMaxM], float2 (*Ab1)[kMaxM], float
 // columns of X are unit vectors to FP32 accuracy (unitary rotations).  Lanes own
 // matrix entries (at most 4 each).  Control flow that contains warp-wide
 // synchronisation is uniform over the warp.
+template <int NE>
 __global__ void __launch_bounds__(kSetupWarps * 32)
 setup_kernel(DevState d, int n_rows, double null_tol) {
     __shared__ double2 sA[kSetupRows][kMaxM][kMaxM];    // R' (symmetrised)
@@ -287,7 +292,7 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     __syncwarp();
 
     // ---- phase 1: FP32 Jacobi sweeps ---------------------------------------------
-    const int jc = jacobi_parallel(sJ[g][0], sJ[g][1], sJ[g][2], sJ[g][3], M, l, afro2, 1e-12f, 1e-14f,
+    const int jc = jacobi_parallel<NE>(sJ[g][0], sJ[g][1], sJ[g][2], sJ[g][3], M, l, afro2, 1e-12f, 1e-14f,
                                    kJacobiMaxSweeps32);
     for (int e = l; e < MM; e += kGroupLanes) {
         const float2 v = sJ[g][2 + jc][e / M][e % M];
@@ -297,18 +302,18 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     __syncwarp();
 
     // ---- phase 2: refinement of the eigenbasis ------------------------------------
-    int ei[kEntries], ej[kEntries];                       // this lane's entries (i, j)
+    int ei[NE], ej[NE];                       // this lane's entries (i, j)
 #pragma unroll
-    for (int t = 0; t < kEntries; ++t) {
+    for (int t = 0; t < NE; ++t) {
         const int e = l + kGroupLanes * t;
         ei[t] = e < MM ? e / M : 0;
         ej[t] = e < MM ? e - (e / M) * M : 0;
     }
     bool done = false;                  // this group's refinement has converged
     for (int step = 0; step < kRefineMaxSteps; ++step) {
-        double2 rv[kEntries], sv[kEntries];
+        double2 rv[NE], sv[NE];
 #pragma unroll
-        for (int t = 0; t < kEntries; ++t) {                     // R = I - X^H X, T = R' X (FP64)
+        for (int t = 0; t < NE; ++t) {                     // R = I - X^H X, T = R' X (FP64)
             const int e = l + kGroupLanes * t;
             if (e < MM) {
                 const int i = ei[t], j = ej[t];
@@ -325,7 +330,7 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
         __syncwarp();
         float so2 = 0.f, rr2 = 0.f;
 #pragma unroll
-        for (int t = 0; t < kEntries; ++t) {                     // S = X^H T (FP64), lambda
+        for (int t = 0; t < NE; ++t) {                     // S = X^H T (FP64), lambda
             const int e = l + kGroupLanes * t;
             if (e < MM) {
                 const int i = ei[t], j = ej[t];
@@ -347,7 +352,7 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
         __syncwarp();
         float emax = 0.f;
 #pragma unroll
-        for (int t = 0; t < kEntries; ++t) {                     // E (FP32)
+        for (int t = 0; t < NE; ++t) {                     // E (FP32)
             const int e = l + kGroupLanes * t;
             if (e < MM) {
                 const int i = ei[t], j = ej[t];
@@ -367,7 +372,7 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
         emax = group_max_f(emax);
         __syncwarp();
 #pragma unroll
-        for (int t = 0; t < kEntries; ++t) {                     // X <- X + X E
+        for (int t = 0; t < NE; ++t) {                     // X <- X + X E
             const int e = l + kGroupLanes * t;
             if (e < MM && !done) {
                 const int i = ei[t], j = ej[t];
@@ -544,10 +549,13 @@ __global__ void __launch_bounds__(kSlotBlock) invariants_kernel(DevState d) {
 
 }  // namespace
 
-cudaError_t launch_setup(const DevState& d, int n_rows, double null_tol, cudaStream_t s) {
+cudaError_t launch_setup(const DevState& d, int n_rows, int max_m, double null_tol, cudaStream_t s) {
     if (n_rows <= 0) return cudaSuccess;
     const int grid = (n_rows + kSetupRows - 1) / kSetupRows;
-    setup_kernel<<<grid, kSetupWarps * 32, 0, s>>>(d, n_rows, null_tol);
+    if (max_m * max_m <= kGroupLanes)
+        setup_kernel<1><<<grid, kSetupWarps * 32, 0, s>>>(d, n_rows, null_tol);
+    else
+        setup_kernel<kMaxEntries><<<grid, kSetupWarps * 32, 0, s>>>(d, n_rows, null_tol);
     return cudaGetLastError();
 }
 
