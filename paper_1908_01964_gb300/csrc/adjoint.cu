@@ -89,7 +89,7 @@ struct AdjShared {
     double2 dP[kMaxM][kMaxM], dG[kMaxM][kMaxM], dT[kMaxM][kMaxM];
     double2 dva[kMaxM], dvb[kMaxM], dga[kMaxM], dgb[kMaxM], dGb[kMaxM];
     double2 dA_[kMaxM], dE[kMaxM][kMaxM];
-    double dmu[kMaxM];
+    double dmu[kMaxM], dimu[kMaxM];
 };
 
 template <int BLOCK, int NP, int SPT>
@@ -109,6 +109,7 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     double2 *dva = sh.dva, *dvb = sh.dvb, *dga = sh.dga, *dgb = sh.dgb, *dGb = sh.dGb, *dA_ = sh.dA_;
     double2(*dE)[kMaxM] = sh.dE;
     double* dmu = sh.dmu;
+    double* dimu = sh.dimu;
 
     const RowDesc* rd = d.rows + r;
     const int J = rd->J;
@@ -120,14 +121,16 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     if (tid < M) {
         s_a[tid] = d.a32[(size_t)r * kMaxM + tid];
         s_b[tid] = d.b32[(size_t)r * kMaxM + tid];
-        dmu[tid] = d.mu[(size_t)r * kMaxM + tid];
+        const double mu = d.mu[(size_t)r * kMaxM + tid];
+        dmu[tid] = mu;
+        dimu[tid] = tid >= 1 ? 1.0 / mu : 0.0;     // 1/mu_i of the nonzero eigenpairs
     }
     for (int e = tid; e < MM; e += BLOCK) dE[e / M][e % M] = d.evec64[(size_t)r * 64 + e];
     __syncthreads();
     for (int e = tid; e < MM; e += BLOCK) {          // P = sum_{i>=2} e_i e_i^H / mu_i (Eq. (eq:riinv))
         const int m = e / M, n = e % M;
         double2 v = make_double2(0.0, 0.0);
-        for (int i = 1; i < M; ++i) v = zadd(v, zscale(zmulc(dE[n][i], dE[m][i]), 1.0 / dmu[i]));
+        for (int i = 1; i < M; ++i) v = zadd(v, zscale(zmulc(dE[n][i], dE[m][i]), dimu[i]));
         dP[m][n] = v;
         s_P[e] = make_float2((float)v.x, (float)v.y);
     }
@@ -466,8 +469,8 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     if (lane < M) {
         double2 pa = make_double2(0.0, 0.0), pva = make_double2(0.0, 0.0);
         for (int n = 0; n < M; ++n) {
-            pa = zadd(pa, zmul(dP[lane][n], dA_[n]));
-            pva = zadd(pva, zmul(dP[lane][n], dva[n]));
+            pa = zfma(pa, dP[lane][n], dA_[n]);
+            pva = zfma(pva, dP[lane][n], dva[n]);
         }
         // g_a = g_a(Wiener) + P v_a + 2 g_taa P a + b conj(g_sab)
         double2 ga = make_double2((double)sh.ga_w[2 * lane], (double)sh.ga_w[2 * lane + 1]);
@@ -491,7 +494,7 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     for (int e = lane; e < MM; e += 32, ++cnt) {            // G E
         const int m = e / M, n = e % M;
         double2 v = make_double2(0.0, 0.0);
-        for (int k = 0; k < M; ++k) v = zadd(v, zmul(dT[m][k], dE[k][n]));
+        for (int k = 0; k < M; ++k) v = zfma(v, dT[m][k], dE[k][n]);
         tmp[cnt] = v;
     }
     __syncwarp();
@@ -501,12 +504,12 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     for (int e = lane; e < MM; e += 32) {                     // G' = E^H (G E)
         const int i = e / M, k = e % M;
         double2 v = make_double2(0.0, 0.0);
-        for (int m = 0; m < M; ++m) v = zadd(v, zmulc(dE[m][i], dG[m][k]));
+        for (int m = 0; m < M; ++m) v = zfma_c(v, dE[m][i], dG[m][k]);
         dT[i][k] = v;
     }
     if (lane < M) {                                           // g' = E^H g_b
         double2 v = make_double2(0.0, 0.0);
-        for (int m = 0; m < M; ++m) v = zadd(v, zmulc(dE[m][lane], dgb[m]));
+        for (int m = 0; m < M; ++m) v = zfma_c(v, dE[m][lane], dgb[m]);
         dGb[lane] = v;
     }
     __syncwarp();
@@ -515,11 +518,11 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
         const int i = e / M, k = e % M;
         double2 f = make_double2(0.0, 0.0);
         if (i >= 1 && k >= 1) {
-            f = zscale(dT[i][k], -1.0 / (dmu[i] * dmu[k]));
+            f = zscale(dT[i][k], -(dimu[i] * dimu[k]));
         } else if (i >= 1 || k >= 1) {
             const int q = i >= 1 ? i : k;
-            const double gap = dmu[q] - mu1;
-            f = zsub(zscale(dT[q][0], 1.0 / (dmu[q] * gap)), zscale(dGb[q], 0.5 / gap));
+            const double igap = 1.0 / (dmu[q] - mu1);
+            f = zsub(zscale(dT[q][0], dimu[q] * igap), zscale(dGb[q], 0.5 * igap));
             if (i == 0) f = zconj(f);
         }
         dG[i][k] = f;
@@ -528,7 +531,7 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     for (int e = lane; e < MM; e += 32) {                     // F E^H
         const int i = e / M, n = e % M;
         double2 v = make_double2(0.0, 0.0);
-        for (int k = 0; k < M; ++k) v = zadd(v, zmul(dG[i][k], zconj(dE[n][k])));
+        for (int k = 0; k < M; ++k) v = zfma(v, dG[i][k], zconj(dE[n][k]));
         dT[i][n] = v;
     }
     __syncwarp();
@@ -536,7 +539,7 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     for (int e = lane; e < MM; e += 32) {                     // E (F E^H)
         const int m = e / M, n = e % M;
         double2 v = make_double2(0.0, 0.0);
-        for (int i = 0; i < M; ++i) v = zadd(v, zmul(dE[m][i], dT[i][n]));
+        for (int i = 0; i < M; ++i) v = zfma(v, dE[m][i], dT[i][n]);
         gR[e] = v;
     }
     if (lane < M) g.grad_a[rd->a_off + lane] = dga[lane];

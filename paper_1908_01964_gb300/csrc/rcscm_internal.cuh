@@ -129,6 +129,17 @@ __device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 zscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double zabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+// acc + a b, acc + conj(a) b and acc - conj(a) b, two fused multiply-adds per component
+// (every FP64 instruction counts on sm_103a).
+__device__ __forceinline__ double2 zfma(double2 acc, double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 zfma_c(double2 acc, double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double2 zfms_c(double2 acc, double2 a, double2 b) {
+    return make_double2(fma(-a.x, b.x, fma(-a.y, b.y, acc.x)), fma(-a.x, b.y, fma(a.y, b.x, acc.y)));
+}
 
 // Hardware reciprocal approximation (MUFU.RCP, relative error ~1 ulp); inputs
 // here are positive normal numbers.

@@ -44,18 +44,6 @@ constexpr int kRefineMaxSteps = 6;
 
 __device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
-// acc + a b, acc + conj(a) b and acc - conj(a) b, two fused multiply-adds per component
-// (every FP64 instruction counts on sm_103a).
-__device__ __forceinline__ double2 zfma(double2 acc, double2 a, double2 b) {
-    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
-}
-__device__ __forceinline__ double2 zfma_c(double2 acc, double2 a, double2 b) {
-    return make_double2(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
-}
-__device__ __forceinline__ double2 zfms_c(double2 acc, double2 a, double2 b) {
-    return make_double2(fma(-a.x, b.x, fma(-a.y, b.y, acc.x)), fma(-a.x, b.y, fma(a.y, b.x, acc.y)));
-}
-
 // Sum / maximum over the 16 lanes of a row group (xor offsets stay in the group).
 __device__ __forceinline__ float group_sum_f(float v) {
 #pragma unroll
