@@ -51,6 +51,9 @@ extern "C" {
 #define RCSCM_ETIMEOUT    7  /* reserved: a bounded device wait gave up            */
 #define RCSCM_ECAPACITY   8  /* the problem does not fit the fixed scratch array of
                                 rcscm_solve_noalloc (nothing was launched)         */
+#define RCSCM_EBOUNDS     9  /* a row, slot or shape index check of the debug build
+                                 (compiled with RCSCM_DEBUG) failed; the offending
+                                 CTA skipped its work.  Never set by the normal build */
 
 /* ---- update rules ------------------------------------------------------ */
 #define RCSCM_RULE_ACCEL  0  /* second-stage accelerated rule, Algorithm 2         */

@@ -1,10 +1,14 @@
 """Build the CUDA shared library (sm_103a) in-tree with nvcc.
 
     python -m paper_1908_01964_gb300.build        # or build() from Python
+    python -m paper_1908_01964_gb300.build --debug   # the index-checking build
 
 Translation units compile in parallel into ``_build/`` and link into
 ``paper_1908_01964_gb300/librcscm.so`` (CUDA runtime linked statically, so the
-library only needs the NVIDIA driver at load time).
+library only needs the NVIDIA driver at load time).  ``build(debug=True)``
+compiles with RCSCM_DEBUG (row, slot and shape checks in every kernel that set
+RCSCM_EBOUNDS instead of touching memory out of range) into ``_build_debug/``
+and ``librcscm_debug.so``.
 """
 from __future__ import annotations
 
@@ -19,6 +23,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librcscm.so")
+LIB_DEBUG = os.path.join(PKG, "librcscm_debug.so")
 SOURCES = ["api.cu", "setup.cu", "iterate.cu", "naive.cu", "extract.cu", "objective.cu", "host.cu", "noalloc.cu", "adjoint.cu", "accel1.cu", "ilrma.cu"]
 # (threads per row, slots per thread) shapes of the accelerated kernels: iterate_inst.cu
 # is compiled once per shape so that the large unrolled kernels build in parallel.
@@ -42,27 +47,31 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = None) -> bool:
+    lib = lib or LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile every translation unit for sm_103a and link librcscm.so; returns its path."""
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra_flags=None, debug: bool = False) -> str:
+    """Compile every translation unit for sm_103a and link librcscm.so (or, with
+    debug, librcscm_debug.so); returns its path."""
+    lib = LIB_DEBUG if debug else LIB
+    build_dir = BUILD_DIR + "_debug" if debug else BUILD_DIR
+    if not force and up_to_date(lib):
+        return lib
     nvcc = nvcc_path()
-    os.makedirs(BUILD_DIR, exist_ok=True)
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    os.makedirs(build_dir, exist_ok=True)
+    flags = NVCC_FLAGS + list(extra_flags or []) + (["-DRCSCM_DEBUG"] if debug else [])
     procs = []
     objs = []
     units = [(src, src.replace(".cu", ".o"), []) for src in SOURCES]
     units += [("iterate_inst.cu", f"iterate_b{b}_s{t}.o", [f"-DRCSCM_INST_BLOCK={b}", f"-DRCSCM_INST_SPT={t}"])
               for b, t in INSTANCES]
     for src, objname, defs in units:
-        obj = os.path.join(BUILD_DIR, objname)
+        obj = os.path.join(build_dir, objname)
         cmd = [nvcc, *ARCH, *flags, *defs, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
@@ -78,15 +87,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if failed:
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     force = "--force" in sys.argv
-    print(build(force=force, verbose="-v" in sys.argv))
+    print(build(force=force, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(BLOCK) accel1_kernel(DevState d, int n_iter, I
     __shared__ float red[2][BLOCK / 32];
     __shared__ float2 sphi[kMaxM * kMaxM];
     const int r = d.order[blockIdx.x];
+    RCSCM_CTA_CHECK(row_ok(d, r, 8 * BLOCK), d.status);
     const int np = (d.rows[r].J + 2 * BLOCK - 1) / (2 * BLOCK);
     switch (np) {
         case 1: accel1_row<BLOCK, 1>(d, r, n_iter, p, red, sphi); break;

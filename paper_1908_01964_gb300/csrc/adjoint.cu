@@ -551,6 +551,7 @@ template <int BLOCK, int SPT>
 __global__ void __launch_bounds__(BLOCK) adjoint_kernel(DevState d, AdjointArgs g, IterParams p) {
     __shared__ AdjShared<BLOCK, SPT> sh;
     const int r = blockIdx.x;
+    RCSCM_CTA_CHECK(row_ok(d, r, BLOCK * SPT), d.status);
     const int np = (d.rows[r].J + 2 * BLOCK - 1) / (2 * BLOCK);
     switch (np) {
         case 1: adjoint_row<BLOCK, 1, SPT>(d, g, p, r, sh); break;

@@ -193,6 +193,7 @@ const char* rcscm_strerror(int code) {
         case RCSCM_ENOMEM: return "device memory allocation failed";
         case RCSCM_ETIMEOUT: return "bounded device wait gave up";
         case RCSCM_ECAPACITY: return "problem too large for the fixed scratch array of rcscm_solve_noalloc";
+        case RCSCM_EBOUNDS: return "an index check of the debug build failed";
         default: return "unknown rcscm status code";
     }
 }
@@ -579,6 +580,7 @@ int rcscm_status(rcscm_ctx* c, int* flags, void* stream) {
     if (e == cudaSuccess) e = cudaMemset(c->d.status, 0, sizeof(int));
     if (e != cudaSuccess) return map_cuda(e);
     if (flags) *flags = h;
+    if (h & kFlagBounds) return RCSCM_EBOUNDS;
     if (h & kFlagNullspace) return RCSCM_ENULLSPACE;
     if (h & kFlagNonfinite) return RCSCM_ENONFINITE;
     if (h & kFlagClamp) return RCSCM_ECLAMP;

@@ -16,6 +16,7 @@ __global__ void __launch_bounds__(kSlotBlock) extract_kernel(DevState d, float2*
     __shared__ float2 sa[kMaxM];
     __shared__ __align__(16) float2 sh[kSlotBlock * kMaxM];
     const BlockMap bm = d.bmap[blockIdx.x];
+    RCSCM_CTA_CHECK(block_ok(d, bm), d.status);
     const RowDesc* rd = d.rows + bm.row;
     const int M = rd->M;
     const int J = rd->J;

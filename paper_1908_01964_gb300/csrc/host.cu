@@ -263,6 +263,7 @@ extern "C" int rcscm_host_run(rcscm_host* p, const void* x, const void* a, const
     if (e != cudaSuccess) return code_of(e);
     const int flags = *p->hstatus;
     *p->hstatus = 0;
+    if (flags & rcscm::kFlagBounds) return RCSCM_EBOUNDS;
     if (flags & rcscm::kFlagNullspace) return RCSCM_ENULLSPACE;
     if (flags & rcscm::kFlagNonfinite) return RCSCM_ENONFINITE;
     if (flags & rcscm::kFlagClamp) return RCSCM_ECLAMP;

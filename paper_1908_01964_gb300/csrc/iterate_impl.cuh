@@ -111,6 +111,7 @@ __device__ __forceinline__ void accel_one_row(const DevState& d, int r, int n_it
 template <int BLOCK, int SPT>
 __global__ void __launch_bounds__(BLOCK) accel_kernel(DevState d, int n_iter, IterParams p) {
     __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
+    RCSCM_CTA_CHECK(row_ok(d, d.order[blockIdx.x], BLOCK * SPT), d.status);
     accel_one_row<BLOCK, SPT, false>(d, d.order[blockIdx.x], n_iter, p, red, nullptr, nullptr);
 }
 
@@ -118,6 +119,7 @@ template <int BLOCK, int SPT>
 __global__ void __launch_bounds__(BLOCK, solve_min_blocks(BLOCK, SPT)) solve_kernel(DevState d, int n_iter, IterParams p, float2* h) {
     __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
     __shared__ FusedSmem fs;
+    RCSCM_CTA_CHECK(row_ok(d, d.order[blockIdx.x], BLOCK * SPT), d.status);
     accel_one_row<BLOCK, SPT, true>(d, d.order[blockIdx.x], n_iter, p, red, h, &fs);
 }
 
@@ -135,6 +137,7 @@ __global__ void __launch_bounds__(BLOCK) accel_persistent_kernel(DevState d, int
         __syncthreads();
         const int k = s_next;
         if (k >= n_rows) break;
+        RCSCM_CTA_CHECK(row_ok(d, d.order[k], BLOCK * SPT), d.status);
         accel_one_row<BLOCK, SPT, false>(d, d.order[k], n_iter, p, red, nullptr, nullptr);
     }
 }
@@ -151,6 +154,7 @@ __global__ void __launch_bounds__(BLOCK, solve_min_blocks(BLOCK, SPT)) solve_per
         __syncthreads();
         const int k = s_next;
         if (k >= n_rows) break;
+        RCSCM_CTA_CHECK(row_ok(d, d.order[k], BLOCK * SPT), d.status);
         accel_one_row<BLOCK, SPT, true>(d, d.order[k], n_iter, p, red, h, &fs);
     }
 }

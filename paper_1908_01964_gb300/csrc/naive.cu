@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kNaiveBlock) naive_kernel(DevState d, const in
     __shared__ Cx<T> sa[M], sb[M];
     __shared__ T red[2][kNaiveBlock / 32];
     const int r = rows[blockIdx.x];
+    RCSCM_CTA_CHECK(row_ok(d, r, 1 << 30) && d.rows[r].M == M, d.status);
     const RowDesc* rd = d.rows + r;
     const int J = rd->J;
     const int64_t off = rd->slot_off;

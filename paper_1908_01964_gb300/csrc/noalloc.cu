@@ -122,6 +122,8 @@ extern "C" int rcscm_solve_noalloc(int64_t I, int64_t J, int64_t M, const void* 
     unsigned char* b = static_cast<unsigned char*>(base);
     DevState d{};
     d.rows = reinterpret_cast<RowDesc*>(b + o_rows);
+    d.n_rows = I;
+    d.n_slots = I * J;
     d.rc = reinterpret_cast<RowConst*>(b + o_rc);
     d.bmap = reinterpret_cast<BlockMap*>(b + o_bmap);
     d.order = reinterpret_cast<int*>(b + o_order);

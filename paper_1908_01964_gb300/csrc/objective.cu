@@ -22,6 +22,7 @@ namespace {
 __global__ void __launch_bounds__(kSlotBlock) objective_kernel(DevState d, float alpha1, float beta) {
     __shared__ double red[kSlotBlock / 32];
     const BlockMap bm = d.bmap[blockIdx.x];
+    RCSCM_CTA_CHECK(block_ok(d, bm), d.status);
     const RowDesc* rd = d.rows + bm.row;
     const int M = rd->M;
     const int J = rd->J;

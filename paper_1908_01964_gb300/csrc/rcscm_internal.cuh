@@ -16,6 +16,26 @@ constexpr int kSlotBlock = 256;   // threads per block of the slot-parallel kern
 constexpr int kFlagNullspace = 1 << (RCSCM_ENULLSPACE - 1);
 constexpr int kFlagNonfinite = 1 << (RCSCM_ENONFINITE - 1);
 constexpr int kFlagClamp = 1 << (RCSCM_ECLAMP - 1);
+constexpr int kFlagBounds = 1 << (RCSCM_EBOUNDS - 1);
+
+// Index checks of the debug build (compiled with -DRCSCM_DEBUG; compute-sanitizer
+// is not available).  RCSCM_CTA_CHECK takes a condition that is uniform over the
+// CTA and is placed before the kernel's first barrier: on failure thread 0 sets the
+// bounds bit of the status word and the whole CTA returns, so no buffer is touched
+// out of range and nothing traps.  The normal build compiles the checks away.
+#ifdef RCSCM_DEBUG
+#define RCSCM_CTA_CHECK(cond, status)                                  \
+    do {                                                               \
+        if (!(cond)) {                                                 \
+            if (threadIdx.x == 0) atomicOr((status), kFlagBounds);     \
+            return;                                                    \
+        }                                                              \
+    } while (0)
+#else
+#define RCSCM_CTA_CHECK(cond, status) \
+    do {                              \
+    } while (0)
+#endif
 
 // One row = one (utterance, frequency bin i).  Rows share nothing in any rule.
 struct RowDesc {
@@ -95,6 +115,18 @@ struct IterParams {
     double c_b_f64;
     int ckpt_first;        // index (since setup) of the first pass of this launch
 };
+
+// Row r lies in the tables and its shape fits a kernel covering max_j frames (the
+// debug build's row check).
+__device__ __forceinline__ bool row_ok(const DevState& d, int r, int max_j) {
+    if (r < 0 || r >= d.n_rows) return false;
+    const RowDesc& q = d.rows[r];
+    return q.M >= 1 && q.M <= kMaxM && q.J >= 1 && q.J <= max_j && q.slot_off >= 0 && q.slot_off + q.J <= d.n_slots;
+}
+// A slot block of a slot-parallel kernel starts inside its row.
+__device__ __forceinline__ bool block_ok(const DevState& d, const BlockMap& bm) {
+    return row_ok(d, bm.row, 1 << 30) && bm.j0 >= 0 && bm.j0 < d.rows[bm.row].J;
+}
 
 // ------------------------------------------------------------------ helpers
 

@@ -246,9 +246,15 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     const int g = threadIdx.x / kGroupLanes;
     const int l = threadIdx.x % kGroupLanes;
     const int r = blockIdx.x * kSetupRows + g;
-    const bool active = r < n_rows;
+    bool active = r < n_rows;
     RowDesc rd;
     if (active) rd = d.rows[r];
+#ifdef RCSCM_DEBUG
+    if (active && !(rd.M >= 1 && rd.M <= kMaxM)) {    // the debug build's shape check (group-uniform)
+        if (l == 0) atomicOr(d.status, kFlagBounds);
+        active = false;
+    }
+#endif
     const int M = active ? rd.M : 0;
     const int MM = M * M;
     double2(*A)[kMaxM] = sA[g];
@@ -504,6 +510,7 @@ __global__ void __launch_bounds__(kSlotBlock) invariants_kernel(DevState d) {
     __shared__ float2 sphi[kMaxM * kMaxM];
     __shared__ __align__(16) float2 sx[kSlotBlock * kMaxM];
     const BlockMap bm = d.bmap[blockIdx.x];
+    RCSCM_CTA_CHECK(block_ok(d, bm), d.status);
     const RowDesc* rd = d.rows + bm.row;
     const int M = rd->M;
     const int J = rd->J;

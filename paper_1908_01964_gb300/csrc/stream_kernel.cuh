@@ -20,6 +20,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) accel_stream_kernel(DevSt
     __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
     __shared__ f32x2 s_am[SPT / 2][BLOCK], s_b[SPT / 2][BLOCK];
     const int r = d.order[blockIdx.x];
+    RCSCM_CTA_CHECK(row_ok(d, r, BLOCK * SPT), d.status);
     const RowDesc* rd = d.rows + r;
     const int J = rd->J;
     const int64_t off = rd->slot_off;

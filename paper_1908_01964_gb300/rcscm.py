@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librcscm.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "rcscm.h")
 
-OK, EINVAL, ENULLSPACE, ENONFINITE, ECLAMP, ECUDA, ENOMEM, ETIMEOUT, ECAPACITY = range(9)
+OK, EINVAL, ENULLSPACE, ENONFINITE, ECLAMP, ECUDA, ENOMEM, ETIMEOUT, ECAPACITY, EBOUNDS = range(10)
 RULE_ACCEL, RULE_NAIVE, RULE_NAIVE_F64, RULE_ACCEL1 = 0, 1, 2, 3
 MAX_M = 8
 MAX_J_ACCEL = 4096

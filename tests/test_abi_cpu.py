@@ -108,3 +108,13 @@ def test_null_context_calls_are_rejected(L):
     assert L.rcscm_extract(None, None, None) == R.EINVAL
     assert L.rcscm_status(None, None, None) == R.EINVAL
     L.rcscm_destroy(None)
+
+
+def test_status_codes_match_the_header():
+    import re
+    from paper_1908_01964_gb300 import rcscm as R
+    src = open(R.HEADER).read()
+    codes = dict((m.group(1), int(m.group(2))) for m in re.finditer(r"#define RCSCM_(E[A-Z]+|OK)\s+(\d+)", src))
+    for name, value in codes.items():
+        assert getattr(R, name) == value, name
+    assert codes["EBOUNDS"] == 9
