@@ -647,10 +647,25 @@ def ilrma_section(probs, R, dev, peaks, flush, stream, case, reps=20):
         nbytes += I * M * 16 + I * M * M * 16 + 2 * I * J * 4                 # a, R', r_h0, r_u0
         slots += I * J
     status = torch.zeros(1, dtype=torch.int32, device=dev)
+    # arguments marshalled once, so the event bracket holds the device work (the
+    # 256 MB flush ahead of it covers the host's enqueueing of the launch)
+    plan = R.IlrmaPlan(utts, status=status)
     for _ in range(3):
-        R.ilrma_init(utts, status=status, stream=stream)
+        plan.run(stream)
     torch.cuda.synchronize()
     ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    # the same call through ilrma_init (outputs allocated and arguments marshalled
+    # per call: the host's share shows when it outlasts the flush)
+    ms_api = []
     for _ in range(reps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -658,19 +673,19 @@ def ilrma_section(probs, R, dev, peaks, flush, stream, case, reps=20):
         R.ilrma_init(utts, status=status, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    t = statistics.median(ms)
+        ms_api.append(e0.elapsed_time(e1))
     achieved = nbytes / (t / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
     traffic, tsrc = profiled_traffic("ilrma_init_kernel", case)
-    return {"ms": t, "launches": len(utts), "slots": slots, "slots_per_s": slots / (t / 1e3),
+    return {"ms": t, "ms_per_api_call": statistics.median(ms_api), "launches": len(utts), "slots": slots,
+            "slots_per_s": slots / (t / 1e3),
             "status": int(status.item()),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "traffic_source": tsrc, "traffic_algorithmic": nbytes,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured burst copy)" if peaks
                          else "fallback 6800 GB/s",
-                         "kernel": "ilrma_init_kernel<M> (one CTA per frequency row) + rhinit_kernel (T V); "
-                                   "L2 flushed before each call; traffic is both kernels' DRAM bytes"}}
+                         "kernel": "ilrma_init_kernel<M>: one CTA per frequency row, then the T V tiles in "
+                                   "the same grid; L2 flushed before each call"}}
 
 
 def adjoint_section(args, R, dev, stream):

@@ -311,9 +311,9 @@ int rcscm_solve_noalloc(int64_t I, int64_t J, int64_t M, const void* x, const vo
  * as they are (lambda_i then starts at the minimum nonzero eigenvalue of R'_i).
  * W_i^{-1} and R'_i are formed in FP64, the frame sums from FP32 products with
  * compensated accumulation.  Inputs and outputs are device memory or page-locked
- * host memory of the calling process; the caller owns them.  The work of every
- * utterance is enqueued on `stream` (one launch per utterance) without
- * synchronising.  Returns RCSCM_EINVAL, before anything is launched, for a bad
+ * host memory of the calling process; the caller owns them, and no output may
+ * overlap an input.  The work of every utterance is enqueued on `stream` (one
+ * launch per utterance) without synchronising.  Returns RCSCM_EINVAL, before anything is launched, for a bad
  * shape (M outside 2..RCSCM_MAX_M, K outside 1..256, n_h outside 0..M-1, I or J
  * below 1) or pointer.  `status` (a device int, or NULL) receives the status bits
  * of rcscm_status: RCSCM_ENULLSPACE's for a singular W_i or a noise output with

@@ -16,8 +16,10 @@
 //               M-1 noise outputs, Eq. (eq:rit) (upper triangle, mirrored);
 //   all warps   r_u0_ij = (1/M) sum_{n != n_h} |w_{i,n}^H x_ij|^2 / d_n.
 //
-// r_h0_ij = sum_k t_ik v_kj (Eq. (eq:rhinit)) is a small product T V of its own
-// (rhinit_kernel, tiles staged in shared memory).
+// r_h0_ij = sum_k t_ik v_kj (Eq. (eq:rhinit)) is a small product T V, made by
+// CTAs of the same grid placed after the rows (tiles of 8 rows x 128 frames, t_ik
+// staged in shared memory): they take the SM slots the rows leave free and those
+// the rows release, so the product costs no launch and no wave of its own.
 //
 // The last line is Eq. (eq:ruinit) in closed form: R'_i = Q D Q^H with Q the
 // columns n != n_h of A_i (full column rank) and D = diag(d_n), and the
@@ -68,6 +70,66 @@ __device__ __forceinline__ void pair_add(float& hi, float& lo, float hi2, float 
 // 1025 rows of a 2048-point STFT in one wave at M <= 4.
 constexpr int ilrma_min_blocks(int M) { return M <= 4 ? 7 : 2; }
 
+// r_h0 = T V (Eq. (eq:rhinit)) as a tiled product, in CTAs of the same grid after
+// the rows: a CTA makes kRhRows rows x kRhCols frames.  The K dimension goes in
+// chunks of kRhK (24 keeps the tile role within the rows' 72-register budget):
+// each thread loads its column of V into registers and its share of the rows'
+// t_ik, both before the first barrier (one round trip per chunk); the t_ik are
+// then read from shared memory four at a time as broadcasts.  Each output sums k
+// in increasing order with fused multiply-adds.
+constexpr int kRhRows = 8, kRhCols = kIlrmaBlock, kRhK = 24;
+constexpr int kRhTPer = (kRhRows * kRhK + kRhCols - 1) / kRhCols;   // t_ik loaded per thread
+
+__device__ void rh_tile(const IlrmaArgs& u, int tile) {
+    __shared__ __align__(16) float sT[kRhRows][kRhK];
+    const int nx = (u.J + kRhCols - 1) / kRhCols;
+    const int i0 = (tile / nx) * kRhRows;
+    const int j = (tile % nx) * kRhCols + threadIdx.x;
+    float acc[kRhRows];
+#pragma unroll
+    for (int r = 0; r < kRhRows; ++r) acc[r] = 0.f;
+    for (int k0 = 0; k0 < u.K; k0 += kRhK) {
+        const int kn = min(kRhK, u.K - k0);
+        float v[kRhK], t[kRhTPer];
+#pragma unroll
+        for (int q = 0; q < kRhTPer; ++q) {
+            const int e = threadIdx.x + q * kRhCols;
+            const int r = e / kRhK, k = e % kRhK;
+            t[q] = (r < kRhRows && i0 + r < u.I && k < kn) ? u.T[(size_t)(i0 + r) * u.K + k0 + k] : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < kRhK; ++k) v[k] = (k < kn && j < u.J) ? u.V[(size_t)(k0 + k) * u.J + j] : 0.f;
+        __syncthreads();                              // the previous chunk of sT is consumed
+#pragma unroll
+        for (int q = 0; q < kRhTPer; ++q) {
+            const int e = threadIdx.x + q * kRhCols;
+            if (e < kRhRows * kRhK) sT[e / kRhK][e % kRhK] = t[q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k4 = 0; k4 < kRhK; k4 += 4) {
+            if (k4 < kn) {
+#pragma unroll
+                for (int r = 0; r < kRhRows; ++r) {
+                    const float4 tr = *reinterpret_cast<const float4*>(&sT[r][k4]);
+                    float a = acc[r];
+                    a = fmaf(tr.x, v[k4], a);
+                    if (k4 + 1 < kn) a = fmaf(tr.y, v[k4 + 1], a);
+                    if (k4 + 2 < kn) a = fmaf(tr.z, v[k4 + 2], a);
+                    if (k4 + 3 < kn) a = fmaf(tr.w, v[k4 + 3], a);
+                    acc[r] = a;
+                }
+            }
+        }
+    }
+    if (j < u.J) {
+#pragma unroll
+        for (int r = 0; r < kRhRows; ++r)
+            if (i0 + r < u.I) u.rh0[(size_t)(i0 + r) * u.J + j] = acc[r];
+    }
+}
+
+
 template <int M>
 __global__ void __launch_bounds__(kIlrmaBlock, ilrma_min_blocks(M)) ilrma_init_kernel(IlrmaArgs u, int* status) {
     constexpr int W2 = 2 * M;                          // columns of [W | I]
@@ -79,6 +141,10 @@ __global__ void __launch_bounds__(kIlrmaBlock, ilrma_min_blocks(M)) ilrma_init_k
     __shared__ double sd[M];
     __shared__ int sbad;
 
+    if ((int)blockIdx.x >= u.I) {                      // a T V tile (uniform over the CTA)
+        rh_tile(u, (int)blockIdx.x - u.I);
+        return;
+    }
     const int i = blockIdx.x;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -185,8 +251,8 @@ __global__ void __launch_bounds__(kIlrmaBlock, ilrma_min_blocks(M)) ilrma_init_k
             }
         }
     }
-    // block sum of the partial powers: compensated FP32 pairs down the warps, the four
-    // warp sums in FP64 (warp f contributes zeros; FP64 is slow on this part)
+    // block sum of the partial powers: compensated FP32 pairs down each warp and across
+    // the warps (warp f contributes zeros), one conversion to FP64 at the end
 #pragma unroll
     for (int n = 0; n < M; ++n) {
         float hi = ps[n], lo = -pc[n];
@@ -200,10 +266,10 @@ __global__ void __launch_bounds__(kIlrmaBlock, ilrma_min_blocks(M)) ilrma_init_k
     }
     __syncthreads();
     if (tid < M) {
-        double s = 0.0;
+        float hi = red[0][tid].x, lo = red[0][tid].y;
 #pragma unroll
-        for (int w = 0; w < kIlrmaWarps; ++w) s += (double)red[w][tid].x + (double)red[w][tid].y;
-        const double d = tid == nh ? 0.0 : s / (double)J;
+        for (int w = 1; w < kIlrmaWarps; ++w) pair_add(hi, lo, red[w][tid].x, red[w][tid].y);
+        const double d = tid == nh ? 0.0 : ((double)hi + (double)lo) / (double)J;
         sd[tid] = d;
         sinvd[tid] = tid == nh ? 0.f : (float)(1.0 / d);
         if (tid != nh && !(d > 0.0)) atomicOr(&sbad, 1);
@@ -263,81 +329,24 @@ __global__ void __launch_bounds__(kIlrmaBlock, ilrma_min_blocks(M)) ilrma_init_k
     }
 }
 
-// r_h0 = T V (Eq. (eq:rhinit)) as a tiled product: a CTA of kRhCols threads makes
-// kRhRows rows x kRhCols frames (many small CTAs in one wave).  The K dimension goes
-// in chunks of kRhK: each thread loads its column of V into registers and its share
-// of the rows' t_ik, both before the first barrier (one round trip per chunk); the
-// t_ik are then read from shared memory four at a time as broadcasts.  Each output
-// sums k in increasing order with fused multiply-adds.
-constexpr int kRhRows = 8, kRhCols = 128, kRhK = 32;
-constexpr int kRhTPer = kRhRows * kRhK / kRhCols;     // t_ik loaded per thread
-
-__global__ void __launch_bounds__(kRhCols) rhinit_kernel(IlrmaArgs u) {
-    __shared__ __align__(16) float sT[kRhRows][kRhK];
-    const int i0 = blockIdx.y * kRhRows;
-    const int j = blockIdx.x * kRhCols + threadIdx.x;
-    float acc[kRhRows];
-#pragma unroll
-    for (int r = 0; r < kRhRows; ++r) acc[r] = 0.f;
-    for (int k0 = 0; k0 < u.K; k0 += kRhK) {
-        const int kn = min(kRhK, u.K - k0);
-        float v[kRhK], t[kRhTPer];
-#pragma unroll
-        for (int q = 0; q < kRhTPer; ++q) {
-            const int e = threadIdx.x + q * kRhCols;
-            const int r = e / kRhK, k = e % kRhK;
-            t[q] = (i0 + r < u.I && k < kn) ? u.T[(size_t)(i0 + r) * u.K + k0 + k] : 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < kRhK; ++k) v[k] = (k < kn && j < u.J) ? u.V[(size_t)(k0 + k) * u.J + j] : 0.f;
-        __syncthreads();                              // the previous chunk of sT is consumed
-#pragma unroll
-        for (int q = 0; q < kRhTPer; ++q) {
-            const int e = threadIdx.x + q * kRhCols;
-            sT[e / kRhK][e % kRhK] = t[q];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k4 = 0; k4 < kRhK; k4 += 4) {
-            if (k4 < kn) {
-#pragma unroll
-                for (int r = 0; r < kRhRows; ++r) {
-                    const float4 tr = *reinterpret_cast<const float4*>(&sT[r][k4]);
-                    float a = acc[r];
-                    a = fmaf(tr.x, v[k4], a);
-                    if (k4 + 1 < kn) a = fmaf(tr.y, v[k4 + 1], a);
-                    if (k4 + 2 < kn) a = fmaf(tr.z, v[k4 + 2], a);
-                    if (k4 + 3 < kn) a = fmaf(tr.w, v[k4 + 3], a);
-                    acc[r] = a;
-                }
-            }
-        }
-    }
-    if (j < u.J) {
-#pragma unroll
-        for (int r = 0; r < kRhRows; ++r)
-            if (i0 + r < u.I) u.rh0[(size_t)(i0 + r) * u.J + j] = acc[r];
-    }
-}
-
 }  // namespace
 
 cudaError_t launch_ilrma_init(const IlrmaArgs& u, int* status, cudaStream_t s) {
     if (u.I <= 0 || u.J <= 0) return cudaSuccess;
+    const long long n_rh = (long long)((u.J + kRhCols - 1) / kRhCols) * ((u.I + kRhRows - 1) / kRhRows);
+    const long long grid = (long long)u.I + n_rh;      // the rows, then the T V tiles
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const unsigned g = (unsigned)grid;
     switch (u.M) {
-        case 2: ilrma_init_kernel<2><<<u.I, kIlrmaBlock, 0, s>>>(u, status); break;
-        case 3: ilrma_init_kernel<3><<<u.I, kIlrmaBlock, 0, s>>>(u, status); break;
-        case 4: ilrma_init_kernel<4><<<u.I, kIlrmaBlock, 0, s>>>(u, status); break;
-        case 5: ilrma_init_kernel<5><<<u.I, kIlrmaBlock, 0, s>>>(u, status); break;
-        case 6: ilrma_init_kernel<6><<<u.I, kIlrmaBlock, 0, s>>>(u, status); break;
-        case 7: ilrma_init_kernel<7><<<u.I, kIlrmaBlock, 0, s>>>(u, status); break;
-        case 8: ilrma_init_kernel<8><<<u.I, kIlrmaBlock, 0, s>>>(u, status); break;
+        case 2: ilrma_init_kernel<2><<<g, kIlrmaBlock, 0, s>>>(u, status); break;
+        case 3: ilrma_init_kernel<3><<<g, kIlrmaBlock, 0, s>>>(u, status); break;
+        case 4: ilrma_init_kernel<4><<<g, kIlrmaBlock, 0, s>>>(u, status); break;
+        case 5: ilrma_init_kernel<5><<<g, kIlrmaBlock, 0, s>>>(u, status); break;
+        case 6: ilrma_init_kernel<6><<<g, kIlrmaBlock, 0, s>>>(u, status); break;
+        case 7: ilrma_init_kernel<7><<<g, kIlrmaBlock, 0, s>>>(u, status); break;
+        case 8: ilrma_init_kernel<8><<<g, kIlrmaBlock, 0, s>>>(u, status); break;
         default: return cudaErrorInvalidValue;
     }
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const dim3 grid((u.J + kRhCols - 1) / kRhCols, (u.I + kRhRows - 1) / kRhRows);
-    rhinit_kernel<<<grid, kRhCols, 0, s>>>(u);
     return cudaGetLastError();
 }
 

@@ -370,6 +370,41 @@ class Solver:
         return dict(rows=r.value, slots=s.value, device_bytes=b.value)
 
 
+class IlrmaPlan:
+    """rcscm_ilrma_init with its arguments marshalled once: the output tensors and
+    the argument array are made at construction, and run() enqueues the call on
+    `stream` (the same outputs are overwritten by every run).  Inputs and status
+    as for ilrma_init; they must stay alive while the plan is used."""
+
+    def __init__(self, utts, status=None):
+        import torch
+        self._arr = (Ilrma * len(utts))()
+        self._keep = list(utts)
+        self.outs = []
+        for k, u in enumerate(utts):
+            I, J, M = u["x"].shape
+            K = u["T"].shape[1]
+            dev = u["x"].device if u["x"].is_cuda else torch.device("cuda", torch.cuda.current_device())
+            o = dict(a=torch.empty((I, M), dtype=torch.complex128, device=dev),
+                     Rp=torch.empty((I, M, M), dtype=torch.complex128, device=dev),
+                     rh0=torch.empty((I, J), dtype=torch.float32, device=dev),
+                     ru0=torch.empty((I, J), dtype=torch.float32, device=dev))
+            q = self._arr[k]
+            q.I, q.J, q.M, q.K, q.n_h = I, J, M, K, int(u.get("n_h", 0))
+            q.x = _dev(u["x"], torch.complex64, (I, J, M), "x")
+            q.W = _dev(u["W"], torch.complex128, (I, M, M), "W")
+            q.T = _dev(u["T"], torch.float32, (I, K), "T")
+            q.V = _dev(u["V"], torch.float32, (K, J), "V")
+            q.a, q.Rp, q.rh0, q.ru0 = (c_void_p(o[n].data_ptr()) for n in ("a", "Rp", "rh0", "ru0"))
+            self.outs.append(o)
+        self._status = status
+        self._st = None if status is None else _dev(status, torch.int32, (1,), "status")
+
+    def run(self, stream=None) -> list:
+        _check(lib().rcscm_ilrma_init(self._arr, len(self.outs), self._st, _stream(stream)), "rcscm_ilrma_init")
+        return self.outs
+
+
 def ilrma_init(utts, status=None, stream=None) -> list:
     """Estimator inputs from the outputs of the ILRMA stage (rcscm_ilrma_init).
 
@@ -380,28 +415,7 @@ def ilrma_init(utts, status=None, stream=None) -> list:
     (float32 [I, J]) as CUDA tensors on the inputs' device, in the layouts
     Solver takes.  `status` (an int32 CUDA tensor of one element, or None)
     receives the status bits.  Enqueued on `stream`; does not synchronise."""
-    import torch
-    arr = (Ilrma * len(utts))()
-    outs = []
-    for k, u in enumerate(utts):
-        I, J, M = u["x"].shape
-        K = u["T"].shape[1]
-        dev = u["x"].device if u["x"].is_cuda else torch.device("cuda", torch.cuda.current_device())
-        o = dict(a=torch.empty((I, M), dtype=torch.complex128, device=dev),
-                 Rp=torch.empty((I, M, M), dtype=torch.complex128, device=dev),
-                 rh0=torch.empty((I, J), dtype=torch.float32, device=dev),
-                 ru0=torch.empty((I, J), dtype=torch.float32, device=dev))
-        q = arr[k]
-        q.I, q.J, q.M, q.K, q.n_h = I, J, M, K, int(u.get("n_h", 0))
-        q.x = _dev(u["x"], torch.complex64, (I, J, M), "x")
-        q.W = _dev(u["W"], torch.complex128, (I, M, M), "W")
-        q.T = _dev(u["T"], torch.float32, (I, K), "T")
-        q.V = _dev(u["V"], torch.float32, (K, J), "V")
-        q.a, q.Rp, q.rh0, q.ru0 = (c_void_p(o[n].data_ptr()) for n in ("a", "Rp", "rh0", "ru0"))
-        outs.append(o)
-    st = None if status is None else _dev(status, torch.int32, (1,), "status")
-    _check(lib().rcscm_ilrma_init(arr, len(utts), st, _stream(stream)), "rcscm_ilrma_init")
-    return outs
+    return IlrmaPlan(utts, status).run(stream)
 
 
 def ilrma_to_device(prob: dict, device="cuda") -> dict:

@@ -118,3 +118,21 @@ def test_ilrma_init_status_and_refusals():
     assert ei.value.code == R.EINVAL
     with pytest.raises(TypeError):                    # pageable host memory: refused by the binding
         R.ilrma_init([dict(d, x=d["x"].cpu())])
+
+
+def test_ilrma_plan_reruns_reproduce_the_call():
+    # a prepared call run again over its own outputs gives the one-shot call's
+    # results bit for bit
+    from paper_1908_01964_gb300 import rcscm as R
+    probs = [_raw(4, 9, 300, 5, 61, n_h=1), _raw(3, 5, 77, 2, 62, n_h=2)]
+    utts = [R.ilrma_to_device(p) for p in probs]
+    ref = [{k: v.cpu().numpy() for k, v in o.items()} for o in R.ilrma_init(utts)]
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    plan = R.IlrmaPlan(utts, status=status)
+    for _ in range(3):
+        outs = plan.run()
+        torch.cuda.synchronize()
+        for o, r in zip(outs, ref):
+            for k in r:
+                np.testing.assert_array_equal(o[k].cpu().numpy(), r[k], err_msg=k)
+    assert int(status.item()) == 0
