@@ -21,15 +21,21 @@ __global__ void __launch_bounds__(kSlotBlock) extract_kernel(DevState d, float2*
     const int M = rd->M;
     const int J = rd->J;
     const int n = min(kSlotBlock, J - bm.j0);            // slots of this block
+    const int t = threadIdx.x;
+    // the slot's state and the row constants, in flight while a_i is staged
+    const RowConst c = d.rc[bm.row];
+    const float lam = d.lam[bm.row];
+    float4 tv = make_float4(0.f, 0.f, 0.f, 0.f);
+    float rh = 0.f, ru = 0.f;
+    if (t < n) {
+        const int64_t s = rd->slot_off + bm.j0 + t;
+        tv = d.inv4[s];
+        rh = d.rh[s];
+        ru = d.ru[s];
+    }
     if (threadIdx.x < M) sa[threadIdx.x] = d.a32[(size_t)bm.row * kMaxM + threadIdx.x];
     __syncthreads();
-    const int t = threadIdx.x;
     if (t < n) {
-        const RowConst c = d.rc[bm.row];
-        const float lam = d.lam[bm.row];
-        const int64_t s = rd->slot_off + bm.j0 + t;
-        const float4 tv = d.inv4[s];
-        const float rh = d.rh[s], ru = d.ru[s];
         const float2 w = wiener_weight(c.taa, c.sab2, make_float2(c.sab_re, c.sab_im), lam, tv, rh, ru);
         for (int m = 0; m < M; ++m) sh[t * M + m] = cmul_exact(w, sa[m]);
     }

@@ -515,6 +515,13 @@ __global__ void __launch_bounds__(kSlotBlock) invariants_kernel(DevState d) {
     const int M = rd->M;
     const int J = rd->J;
     const int n = min(kSlotBlock, J - bm.j0);            // slots of this block
+    const int t = threadIdx.x;
+    const int j = bm.j0 + t;
+    float rh0 = 0.f, ru0 = 0.f;                        // in flight while x is staged
+    if (t < n) {
+        rh0 = rd->rh0[j];
+        ru0 = rd->ru0[j];
+    }
     for (int e = threadIdx.x; e < M * M; e += blockDim.x) sphi[e] = d.phi[(size_t)bm.row * 64 + e];
     // stage the block's x (n * M complex, contiguous) with coalesced 16-byte loads when aligned
     const float2* src = rd->x + (size_t)bm.j0 * M;
@@ -528,9 +535,7 @@ __global__ void __launch_bounds__(kSlotBlock) invariants_kernel(DevState d) {
         for (int e = threadIdx.x; e < nc; e += blockDim.x) sx[e] = src[e];
     }
     __syncthreads();
-    const int t = threadIdx.x;
     if (t >= n) return;
-    const int j = bm.j0 + t;
     const float2* xs = sx + t * M;
     float4 o;
     float kap;
@@ -538,8 +543,8 @@ __global__ void __launch_bounds__(kSlotBlock) invariants_kernel(DevState d) {
     const int64_t s = rd->slot_off + j;
     d.inv4[s] = o;
     d.kap[s] = kap;
-    d.rh[s] = rd->rh0[j];
-    d.ru[s] = rd->ru0[j];
+    d.rh[s] = rh0;
+    d.ru[s] = ru0;
 }
 
 }  // namespace
