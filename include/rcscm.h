@@ -41,7 +41,8 @@ extern "C" {
 /* ---- status codes ------------------------------------------------------ */
 #define RCSCM_OK          0
 #define RCSCM_EINVAL      1  /* bad shape, pointer, option or call order          */
-#define RCSCM_ENULLSPACE  2  /* R'_i is not rank M-1 within options.null_tol      */
+#define RCSCM_ENULLSPACE  2  /* R'_i is not rank M-1 within options.null_tol, or a
+                                caller-supplied b_i is not its null vector          */
 #define RCSCM_ENONFINITE  3  /* a NaN/Inf or non-positive lambda_i was produced   */
 #define RCSCM_ECLAMP      4  /* warning: some r^(u) reached options.ru_floor, or a
                                 naive-rule r^(h) estimate fell below zero in FP32 and
@@ -57,12 +58,23 @@ extern "C" {
 
 /* ---- update rules ------------------------------------------------------ */
 #define RCSCM_RULE_ACCEL  0  /* second-stage accelerated rule, Algorithm 2         */
-#define RCSCM_RULE_NAIVE  1  /* naive rule, Eqs. (eq:rijx)-(eq:M_ru), FP32 arithmetic */
-#define RCSCM_RULE_NAIVE_F64 2 /* naive rule in FP64 arithmetic (state kept in FP32)  */
+#define RCSCM_RULE_NAIVE  1  /* naive rule, Eqs. (eq:rijx)-(eq:M_ru), FP32 arithmetic per slot:
+                                the explicit M x M inverse of every slot's model covariance
+                                is taken in the whitened coordinates of R~_i (a per-row FP64
+                                congruence with R~_i -> I), where the E-step and M-step
+                                formulas are evaluated as printed                      */
+#define RCSCM_RULE_NAIVE_F64 2 /* naive rule in FP64 arithmetic, printed coordinates (state
+                                kept in FP32)                                           */
 #define RCSCM_RULE_ACCEL1 3  /* first-stage accelerated rule, Algorithm 1: the per-slot
                                 quadratic forms with the per-frequency inverses are
                                 re-evaluated from x at every pass (O(M^2) per slot),
                                 rows of up to 4096 frames                             */
+#define RCSCM_RULE_NAIVE_PRINTED 4 /* naive rule in FP32 in the printed coordinates (the
+                                per-slot inverse of R~^(x)_ij itself, then R~ P R~ etc.).
+                                Kept to time the literal form: FP32 rounding in the
+                                ill-conditioned R~ P R~ and r~_h^2 a^H P a terms costs it
+                                1e-4 to 1e-2 relative error after one pass, and it relies
+                                on the RCSCM_ECLAMP projections                         */
 
 #define RCSCM_MAX_M       8  /* largest supported number of microphones          */
 #define RCSCM_MAX_J_ACCEL 4096 /* longest row (frames) of the accelerated kernel  */
@@ -80,16 +92,27 @@ typedef struct {
     int64_t I, J, M;
     const void*   x;        /* complex64  [I][J][M]  observed STFT x_ij                 */
     const void*   a;        /* complex128 [I][M]     steering vector a_i^(h)            */
-    const void*   Rp;       /* complex128 [I][M][M]  R'_i^(u), Hermitian, rank M-1      */
+    const void*   Rp;       /* complex128 [I][M][M]  R'_i^(u), Hermitian, rank M-1
+                               (complex64 when rp_c64 = 1)                               */
     const double* lambda0;  /* [I] initial lambda_i, or NULL: the smallest nonzero
                                eigenvalue of R'_i (Sec. II-B-3)                          */
     const float*  rh0;      /* [I][J] initial r^(h)_ij (Eq. (eq:rhinit)), > 0            */
     const float*  ru0;      /* [I][J] initial r^(u)_ij (Eq. (eq:ruinit)), > 0            */
+    const void*   b;        /* complex128 [I][M] the caller's unit null vector b_i of R'_i,
+                               or NULL.  When given it is validated against the setup's
+                               eigendecomposition (|R'_i b_i| <= 1e-6 |R'_i|_F |b_i| and
+                               |b_i^H e_1| >= (1 - 1e-6) |b_i|, e_1 the eigenvector of the
+                               smallest eigenvalue); a row that fails sets RCSCM_ENULLSPACE
+                               in the status word.  The estimator uses e_1 either way, so
+                               results do not depend on the phase the caller chose.      */
+    int           rp_c64;   /* 0: Rp is complex128 (default); 1: Rp is complex64, read and
+                               widened to FP64 by the setup                               */
 } rcscm_problem;
 
 typedef struct {
     int    rule;             /* RCSCM_RULE_ACCEL (default), RCSCM_RULE_NAIVE,
-                                RCSCM_RULE_NAIVE_F64 or RCSCM_RULE_ACCEL1               */
+                                RCSCM_RULE_NAIVE_F64, RCSCM_RULE_ACCEL1 or
+                                RCSCM_RULE_NAIVE_PRINTED                                */
     double alpha;            /* inverse-gamma shape, Table II: 1.1                      */
     double beta;             /* inverse-gamma scale, Table II: 1e-16                    */
     float  ru_floor;         /* lower bound applied to r^(u) (default FLT_MIN)          */
@@ -268,18 +291,25 @@ int rcscm_solve_host(int64_t I, int64_t J, int64_t M, const void* x, const void*
  * For callers that cannot call cudaMalloc: a real-time audio thread, where an
  * allocation may synchronise the device and stall for an unbounded time, or a
  * host application that hands the library a fixed GPU memory budget and does
- * not let it allocate more.  The caller passes device inputs (x, a, Rp,
- * lambda0 (may be NULL), rh0, ru0, same layouts as rcscm_problem) and device
+ * not let it allocate more.  The caller passes inputs (x, a, Rp, lambda0 (may
+ * be NULL), rh0, ru0, same layouts as rcscm_problem, complex128 Rp) and
  * outputs: rh, ru [I][J] float (may alias rh0, ru0), lambda [I] float, h_out
- * complex64 [I][J][M], and status (a device int that receives the status bits
- * of rcscm_status, or NULL).  The work is the same as rcscm_create +
- * rcscm_setup + rcscm_iterate(n_iter) + rcscm_extract with opt->rule =
- * RCSCM_RULE_ACCEL (other rules: EINVAL), enqueued on `stream`; the call does
- * not synchronise and never calls cudaMalloc, cudaFree or any allocating
+ * complex64 [I][J][M], and status (an int that receives the status bits of
+ * rcscm_status, or NULL).  Each is device memory of the current device or
+ * page-locked host memory, as for rcscm_create; any other address (pageable
+ * host memory, another device's memory) returns EINVAL before anything is
+ * launched.  The work is the same as rcscm_create + rcscm_setup +
+ * rcscm_iterate(n_iter) + rcscm_extract with opt->rule = RCSCM_RULE_ACCEL and
+ * the options block and iters_per_launch; other rules, persistent != 0 and
+ * ckpt_stride != 0 return EINVAL.  The work is enqueued on `stream`; the call
+ * does not synchronise and never calls cudaMalloc, cudaFree or any allocating
  * routine.
  *
  * Working memory comes from one 32 MiB array in the library's device memory,
- * reserved on every GPU that loads the library until the process exits.  A
+ * reserved on every GPU that loads the library's module until the process
+ * exits.  With lazy module loading (the CUDA default) the module, and with it
+ * the array, is loaded by the first call on each device; if the device has no
+ * room for it that call returns RCSCM_ENOMEM.  A
  * problem needs about 1.5 KB per frequency bin plus 20 B per slot (I*J): for
  * example I = 1025, J = 1000 (about 22 MB) fits and I = 2049, J = 4000 does
  * not.  A problem that does not fit returns RCSCM_ECAPACITY before anything is

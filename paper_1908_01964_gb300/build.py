@@ -24,7 +24,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librcscm.so")
 LIB_DEBUG = os.path.join(PKG, "librcscm_debug.so")
-SOURCES = ["api.cu", "setup.cu", "iterate.cu", "naive.cu", "extract.cu", "objective.cu", "host.cu", "noalloc.cu", "adjoint.cu", "accel1.cu", "ilrma.cu"]
+SOURCES = ["api.cu", "setup.cu", "iterate.cu", "naive.cu", "extract.cu", "objective.cu", "host.cu", "noalloc.cu", "adjoint.cu", "accel1.cu", "ilrma.cu", "probe.cu"]
 # (threads per row, slots per thread) shapes of the accelerated kernels: iterate_inst.cu
 # is compiled once per shape so that the large unrolled kernels build in parallel.
 INSTANCES = [(32, 4), (32, 8), (64, 4), (64, 8), (128, 4), (128, 8), (256, 4), (256, 8), (512, 4), (512, 8),
@@ -43,7 +43,7 @@ def nvcc_path() -> str:
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES + ["iterate_inst.cu"]]
     files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
-    files.append(os.path.join(INCLUDE, "rcscm.h"))
+    files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return files
 
 

@@ -85,7 +85,7 @@ void free_all(rcscm_ctx* c) {
 
 int valid_options(const rcscm_options* o) {
     if (o->rule != RCSCM_RULE_ACCEL && o->rule != RCSCM_RULE_NAIVE && o->rule != RCSCM_RULE_NAIVE_F64 &&
-        o->rule != RCSCM_RULE_ACCEL1)
+        o->rule != RCSCM_RULE_ACCEL1 && o->rule != RCSCM_RULE_NAIVE_PRINTED)
         return 0;
     if (!(o->alpha > -2.0) || !(o->beta >= 0.0)) return 0;
     if (!(o->null_tol > 0.0) || !(o->ru_floor >= 0.0f)) return 0;
@@ -140,6 +140,8 @@ int device_view(T* p, T** out) {
 }
 
 }  // namespace
+
+int rcscm::caller_view(const void* p, const void** out) { return device_view(p, out); }
 
 int* rcscm::ctx_status_word(rcscm_ctx* c) { return c ? c->d.status : nullptr; }
 
@@ -210,11 +212,12 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
         const rcscm_problem& q = probs[p];
         if (q.I < 1 || q.J < 1 || q.M < 2 || q.M > kMaxM) return RCSCM_EINVAL;
         if (!q.x || !q.a || !q.Rp || !q.rh0 || !q.ru0) return RCSCM_EINVAL;
+        if (q.rp_c64 != 0 && q.rp_c64 != 1) return RCSCM_EINVAL;
         const void* v;
         const double* vd;
         const float* vf;
         if (device_view(q.x, &v) || device_view(q.a, &v) || device_view(q.Rp, &v) || device_view(q.rh0, &vf) ||
-            device_view(q.ru0, &vf) || (q.lambda0 && device_view(q.lambda0, &vd)))
+            device_view(q.ru0, &vf) || (q.lambda0 && device_view(q.lambda0, &vd)) || (q.b && device_view(q.b, &v)))
             return RCSCM_EINVAL;
         if (q.J > INT32_MAX / 2) return RCSCM_EINVAL;
         if (opt->rule == RCSCM_RULE_ACCEL && q.J > accel_max_j(opt->block)) return RCSCM_EINVAL;
@@ -257,6 +260,7 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
         device_view(q.rh0, &qv.rh0);
         device_view(q.ru0, &qv.ru0);
         if (q.lambda0) device_view(q.lambda0, &qv.lambda0);
+        if (q.b) device_view(q.b, &qv.b);
         c->row0.push_back(r);
         c->slot0.push_back(s);
         c->out0.push_back(o);
@@ -269,7 +273,9 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
             rd.rp_off = po;
             rd.x = static_cast<const float2*>(qv.x) + i * q.J * q.M;
             rd.a = static_cast<const double2*>(qv.a) + i * q.M;
-            rd.Rp = static_cast<const double2*>(qv.Rp) + i * q.M * q.M;
+            rd.Rp = q.rp_c64 ? nullptr : static_cast<const double2*>(qv.Rp) + i * q.M * q.M;
+            rd.Rp_c64 = q.rp_c64 ? static_cast<const float2*>(qv.Rp) + i * q.M * q.M : nullptr;
+            rd.b_in = qv.b ? static_cast<const double2*>(qv.b) + i * q.M : nullptr;
             rd.lambda0 = qv.lambda0 ? qv.lambda0 + i : nullptr;
             rd.rh0 = qv.rh0 + i * q.J;
             rd.ru0 = qv.ru0 + i * q.J;
@@ -327,6 +333,8 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
     if (!st) st = dalloc(c, &d.a32, Rz * kMaxM);
     if (!st) st = dalloc(c, &d.b32, Rz * kMaxM);
     if (!st) st = dalloc(c, &d.rp32, Rz * 64);
+    if (!st) st = dalloc(c, &d.wht32, Rz * 64);
+    if (!st) st = dalloc(c, &d.aw64, Rz * kMaxM);
     if (!st) st = dalloc(c, &d.inv4, Sz);
     if (!st) st = dalloc(c, &d.kap, Sz);
     if (!st) st = dalloc(c, &d.rh, Sz);
@@ -360,7 +368,11 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
         if (!st) st = dalloc(c, &c->seg_ru, Sz * seg);
         if (!st) st = dalloc(c, &c->seg_lam, Rz * seg);
     }
-    if (!st && opt->rule == RCSCM_RULE_NAIVE) {
+    if (!st && opt->rule == RCSCM_RULE_NAIVE) {            // two values per slot
+        float* q = nullptr;
+        st = dalloc(c, &q, (size_t)naive_scratch);
+        d.ru_hat = q;
+    } else if (!st && opt->rule == RCSCM_RULE_NAIVE_PRINTED) {
         float* q = nullptr;
         st = dalloc(c, &q, (size_t)naive_scratch);
         d.ru_hat = q;
@@ -423,8 +435,7 @@ int rcscm_iterate(rcscm_ctx* c, int n_iter, void* stream) {
         else if (c->opt.rule == RCSCM_RULE_ACCEL1)
             e = launch_accel1(c->d, (int)c->R, c->max_j, k, p, cs);
         else
-            e = launch_naive(c->d, c->naive_rows, c->count_by_m, c->first_by_m, k, p,
-                             c->opt.rule == RCSCM_RULE_NAIVE_F64, cs);
+            e = launch_naive(c->d, c->naive_rows, c->count_by_m, c->first_by_m, k, p, c->opt.rule, cs);
         if (e != cudaSuccess) return map_cuda(e);
         const int blk = c->opt.block;
         c->iter_block = (c->iters_done == 0 || c->iter_block == blk) ? blk : -1;
@@ -767,6 +778,7 @@ int rcscm_solve_host(int64_t I, int64_t J, int64_t M, const void* x, const void*
     rcscm_ctx* c = nullptr;
     if (!st) {
         rcscm_problem q;
+        memset(&q, 0, sizeof(q));
         q.I = I; q.J = J; q.M = M;
         q.x = dx; q.a = da; q.Rp = dR; q.lambda0 = dl; q.rh0 = drh; q.ru0 = dru;
         st = rcscm_create(&c, &q, 1, opt, nullptr);

@@ -124,7 +124,7 @@ extern "C" int rcscm_host_create(rcscm_host** out, int64_t I, int64_t J, int64_t
         return code_of(e);
     }
     for (int c = 0; c <= p->n_chunks; ++c) p->i0.push_back(I * c / p->n_chunks);
-    rcscm_problem q;
+    rcscm_problem q = {};
     q.I = I;
     q.J = J;
     q.M = M;

@@ -8,10 +8,12 @@
 // All working memory the solve needs beyond the caller's inputs and outputs
 // (row tables, per-frequency constants, per-slot invariants, status word)
 // lives in one file-scope device array of kNoAllocScratchBytes.  Every GPU that
-// loads this library reserves that array for the life of the process.  Host
-// code cannot use the array's name as a device address, so the first call on
-// each device looks the address up with cudaGetSymbolAddress (with that device
-// current) and caches it; make that first call before any stream capture.
+// loads this library's module reserves that array for the life of the process;
+// with lazy module loading (the CUDA default) that happens at the first call on
+// the device.  Host code cannot use the array's name as a device address, so the
+// first call on each device looks the address up with cudaGetSymbolAddress (with
+// that device current; it loads the module if needed) and caches it; make that
+// first call before any stream capture.
 // Every call on a device shares the one array and leaves its contents behind;
 // the parts that must start at zero are cleared by each call.  Calls whose work
 // overlaps on the GPU (for example on two streams of the same device) race on
@@ -39,8 +41,15 @@ int scratch_address(void** out) {
     if (dev < 0 || dev >= kNoAllocMaxDevices) return RCSCM_EINVAL;
     std::lock_guard<std::mutex> lock(g_addr_mu);
     if (!g_addr[dev]) {
+        // With lazy module loading the first lookup on a device also loads the module,
+        // which places the array in device memory: running out of memory there is ENOMEM.
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RCSCM_ECUDA;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return RCSCM_ENOMEM;
+        }
+        if (e != cudaSuccess || !p) return RCSCM_ECUDA;
         g_addr[dev] = p;
     }
     *out = g_addr[dev];
@@ -72,6 +81,8 @@ __global__ void fill_tables_kernel(DevState d, int I, int J, int M, int nbpr, co
             rd.x = x + (int64_t)t * J * M;
             rd.a = a + (int64_t)t * M;
             rd.Rp = Rp + (int64_t)t * M * M;
+            rd.Rp_c64 = nullptr;
+            rd.b_in = nullptr;
             rd.lambda0 = lambda0 ? lambda0 + t : nullptr;
             rd.rh0 = rh0 + (int64_t)t * J;
             rd.ru0 = ru0 + (int64_t)t * J;
@@ -100,6 +111,7 @@ extern "C" int rcscm_solve_noalloc(int64_t I, int64_t J, int64_t M, const void* 
         return RCSCM_EINVAL;
     if (opt->rule != RCSCM_RULE_ACCEL || opt->iters_per_launch < 0 || !(opt->alpha > -2.0) || !(opt->beta >= 0.0))
         return RCSCM_EINVAL;
+    if (opt->persistent != 0 || opt->ckpt_stride != 0) return RCSCM_EINVAL;   // not offered here
     if (!accel_block_ok(opt->block)) return RCSCM_EINVAL;
     if (I < 1 || J < 1 || M < 2 || M > kMaxM) return RCSCM_EINVAL;
     if (J > accel_max_j(opt->block)) return RCSCM_EINVAL;
@@ -115,6 +127,29 @@ extern "C" int rcscm_solve_noalloc(int64_t I, int64_t J, int64_t M, const void* 
     const size_t o_b32 = cv.take<float2>(R * kMaxM), o_rp32 = cv.take<float2>(R * 64);
     const size_t o_inv4 = cv.take<float4>(S), o_kap = cv.take<float>(S), o_status = cv.take<int>(1);
     if (cv.off > kNoAllocScratchBytes || R * nbpr > (size_t)INT32_MAX) return RCSCM_ECAPACITY;
+
+    // Every caller address must be one this device can reach (the check allocates
+    // nothing); a pageable host buffer or another device's memory is refused here
+    // rather than faulting in a kernel.
+    const void* in[6] = {x, a, Rp, rh0, ru0, lambda0};
+    void* outp[5] = {rh, ru, lambda, h_out, status};
+    const void* vin[6] = {};
+    const void* vout[5] = {};
+    for (int k = 0; k < 6; ++k)
+        if ((in[k] || k < 5) && caller_view(in[k], &vin[k])) return RCSCM_EINVAL;
+    for (int k = 0; k < 5; ++k)
+        if ((outp[k] || k < 4) && caller_view(outp[k], &vout[k])) return RCSCM_EINVAL;
+    x = vin[0];
+    a = vin[1];
+    Rp = vin[2];
+    rh0 = static_cast<const float*>(vin[3]);
+    ru0 = static_cast<const float*>(vin[4]);
+    lambda0 = static_cast<const double*>(vin[5]);
+    rh = static_cast<float*>(const_cast<void*>(vout[0]));
+    ru = static_cast<float*>(const_cast<void*>(vout[1]));
+    lambda = static_cast<float*>(const_cast<void*>(vout[2]));
+    h_out = const_cast<void*>(vout[3]);
+    status = static_cast<int*>(const_cast<void*>(vout[4]));
 
     void* base = nullptr;
     int st = scratch_address(&base);

@@ -46,7 +46,9 @@ struct RowDesc {
     int64_t rp_off;         // first element of the row in concatenated [I][M][M] arrays (grad_Rp)
     const float2* x;        // row start in the caller's x  (J x M complex64)
     const double2* a;       // caller's a_i                 (M complex128)
-    const double2* Rp;      // caller's R'_i                (M x M complex128)
+    const double2* Rp;      // caller's R'_i                (M x M complex128), or nullptr
+    const float2* Rp_c64;   // caller's R'_i given as complex64, or nullptr
+    const double2* b_in;    // caller's b_i to validate (M complex128), or nullptr
     const double* lambda0;  // caller's lambda_i or nullptr
     const float* rh0;       // caller's r^(h)_i.  (J floats)
     const float* ru0;       // caller's r^(u)_i.  (J floats)
@@ -87,7 +89,10 @@ struct DevState {
     float2* phi;           // [R][8][8]  rows: (R'^+ a)^H, Householder complement, b^H
     float2* a32;           // [R][8]
     float2* b32;           // [R][8]
-    float2* rp32;          // [R][8][8]  (naive rule)
+    float2* rp32;          // [R][8][8]  (naive rule, printed coordinates)
+    float2* wht32;         // [R][8][8]  whitening rows (naive rule): row 0 b^H, row k >= 1
+                           //            e_k^H / sqrt(mu_k), e_k the eigenvectors of R' (ascending)
+    double2* aw64;         // [R][8]     whitened steering vector a_k = e_k^H a / sqrt(mu_k), k >= 1
     double2* evec64;       // [R][64] eigenvectors of R', entry m * M + i = e_i[m], ascending (adjoint), or nullptr
     float* ckpt_rh;        // checkpoints written by the accelerated kernel when ckpt_stride > 0:
     float* ckpt_ru;        //   the state entering pass k * ckpt_stride, [k][S] and [k][R]
@@ -115,6 +120,15 @@ struct IterParams {
     double c_b_f64;
     int ckpt_first;        // index (since setup) of the first pass of this launch
 };
+
+// Entry e (row-major, m * M + n) of the caller's R'_i, in FP64 whatever its input type.
+__device__ __forceinline__ double2 rp_entry(const RowDesc& q, int e) {
+    if (q.Rp_c64) {
+        const float2 v = q.Rp_c64[e];
+        return make_double2((double)v.x, (double)v.y);
+    }
+    return q.Rp[e];
+}
 
 // Row r lies in the tables and its shape fits a kernel covering max_j frames (the
 // debug build's row check).
@@ -289,6 +303,11 @@ struct AdjointArgs {
 
 // Launchers (defined in the .cu files, called by the C ABI in api.cu).
 namespace rcscm {
+// The address under which the current device reaches caller memory p (api.cu): device
+// or managed memory of this device as is, page-locked host memory through its device
+// view.  RCSCM_EINVAL for anything else (pageable host memory, another device, an
+// invalid address, NULL); allocates nothing.
+int caller_view(const void* p, const void** out);
 // Device status word of a context (api.cu), for the host pipeline's asynchronous status reads.
 int* ctx_status_word(rcscm_ctx* c);
 // The fused form (rcscm_run) on rows [first_row, first_row + n_rows) of a context in the
@@ -313,8 +332,10 @@ cudaError_t launch_objective(const DevState& d, int n_blocks, const IterParams& 
                              const int* first_block, int n_probs, double* out, cudaStream_t s);
 // rows_by_m: device list of row indices grouped by M; count_by_m / first_by_m:
 // host arrays indexed by M (size kMaxM + 1) giving each group's size and start.
+// rule: RCSCM_RULE_NAIVE (FP32, whitened coordinates), RCSCM_RULE_NAIVE_F64 or
+// RCSCM_RULE_NAIVE_PRINTED (FP64 / FP32 in the printed coordinates).
 cudaError_t launch_naive(const DevState& d, const int* rows_by_m, const int* count_by_m,
-                         const int* first_by_m, int n_iter, const IterParams& p, bool f64, cudaStream_t s);
+                         const int* first_by_m, int n_iter, const IterParams& p, int rule, cudaStream_t s);
 cudaError_t launch_extract(const DevState& d, int n_blocks, float2* h_out, cudaStream_t s);
 // First-stage rule (accel1.cu): threads per row for rows of up to max_j frames (0: too long).
 int accel1_block(int max_j);

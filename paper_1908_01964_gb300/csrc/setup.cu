@@ -50,6 +50,12 @@ __device__ __forceinline__ float group_sum_f(float v) {
     for (int o = kGroupLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+// The same sum where only this row's group takes part (mask = the group's 16 lanes).
+__device__ __forceinline__ float group_sum_masked(float v, unsigned mask) {
+#pragma unroll
+    for (int o = kGroupLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
 __device__ __forceinline__ float group_max_f(float v) {
 #pragma unroll
     for (int o = kGroupLanes / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -266,8 +272,8 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     float afro2 = 0.f;
     for (int e = l; e < MM; e += kGroupLanes) {
         const int m = e / M, n = e % M;
-        const double2 amn = rd.Rp[m * M + n];
-        const double2 anm = rd.Rp[n * M + m];
+        const double2 amn = rp_entry(rd, m * M + n);
+        const double2 anm = rp_entry(rd, n * M + m);
         const double2 h = make_double2(0.5 * (amn.x + anm.x), 0.5 * (amn.y - anm.y));
         A[m][n] = h;
         const float2 hf = to_f2(h);
@@ -424,13 +430,47 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     }
     __syncwarp(gmask);
 
+    // whitening rows of R~_i = R' + lambda~ b b^H for the naive rule: G_0 = b^H (scaled by
+    // 1/sqrt(lambda~) at each pass), G_k = e_k^H / sqrt(mu_k) (k >= 1), so G R~ G^H = I; and
+    // the fixed part of the whitened steering vector, (G a)_k = c_k / sqrt(mu_k)
+    if (d.wht32) {
+        for (int e = l; e < MM; e += kGroupLanes) {
+            const int kk = e / M, n = e % M;
+            const double2 v = kk == 0 ? zconj(X[n][k0]) : zscale(zconj(X[n][perm[kk]]), srs[g][kk]);
+            d.wht32[(size_t)r * 64 + e] = to_f2(v);
+        }
+        if (l < M) d.aw64[(size_t)r * kMaxM + l] = l == 0 ? make_double2(0.0, 0.0) : zscale(sc[g][l], srs[g][l]);
+    }
+    // a caller-supplied null vector b must be the eigenvector of the smallest eigenvalue
+    // (Sec. II-B-1): |R' b| <= 1e-6 |R'|_F |b| and |b^H e_1| >= (1 - 1e-6) |b|
+    bool bad_b = false;
+    if (rd.b_in) {
+        float rb2 = 0.f, bb2 = 0.f, ov_re = 0.f, ov_im = 0.f;
+        if (l < M) {
+            double2 rb = make_double2(0.0, 0.0);
+            for (int n = 0; n < M; ++n) rb = zfma(rb, A[l][n], rd.b_in[n]);
+            const double2 bl = rd.b_in[l];
+            const double2 ov = zmulc(bl, X[l][k0]);
+            rb2 = (float)zabs2(rb);
+            bb2 = (float)zabs2(bl);
+            ov_re = (float)ov.x;
+            ov_im = (float)ov.y;
+        }
+        rb2 = group_sum_masked(rb2, gmask);
+        bb2 = group_sum_masked(bb2, gmask);
+        ov_re = group_sum_masked(ov_re, gmask);
+        ov_im = group_sum_masked(ov_im, gmask);
+        const float t = 1.f - 1e-6f;
+        bad_b = !(bb2 > 0.f) || !(rb2 <= 1e-12f * afro2 * bb2) || !(ov_re * ov_re + ov_im * ov_im >= t * t * bb2);
+    }
+
     double taa = 0.0;                          // tau^(aa) = sum_i |c_i|^2 / mu_i
     for (int i = 1; i < M; ++i) taa = fma(sc[g][i].x, sf[g][i].x, fma(sc[g][i].y, sf[g][i].y, taa));
     double2 sab = make_double2(0.0, 0.0);
     for (int m = 0; m < M; ++m) sab = zfma_c(sab, sa[g][m], X[m][k0]);
 
     const bool bad = !(mu2 > 0.0) || !(fabs(mu1) <= null_tol * muM) || !(taa > 0.0);
-    if (l == 0 && bad) atomicOr(d.status, kFlagNullspace);
+    if (l == 0 && (bad || bad_b)) atomicOr(d.status, kFlagNullspace);
     const double lam0 = rd.lambda0 ? rd.lambda0[0] : mu2;
 
     // Householder vector for u = v / |v|, v_i = c_{i+1} / sqrt(mu_{i+1}), i = 0..M-2

@@ -21,7 +21,9 @@ LIB_PATH = os.path.join(_HERE, "librcscm.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "rcscm.h")
 
 OK, EINVAL, ENULLSPACE, ENONFINITE, ECLAMP, ECUDA, ENOMEM, ETIMEOUT, ECAPACITY, EBOUNDS = range(10)
-RULE_ACCEL, RULE_NAIVE, RULE_NAIVE_F64, RULE_ACCEL1 = 0, 1, 2, 3
+RULE_ACCEL, RULE_NAIVE, RULE_NAIVE_F64, RULE_ACCEL1, RULE_NAIVE_PRINTED = 0, 1, 2, 3, 4
+RULES = {"accel": RULE_ACCEL, "naive": RULE_NAIVE, "naive64": RULE_NAIVE_F64, "accel1": RULE_ACCEL1,
+         "naive_printed": RULE_NAIVE_PRINTED}
 MAX_M = 8
 MAX_J_ACCEL = 4096
 FLT_MIN = float(np.finfo(np.float32).tiny)
@@ -30,7 +32,8 @@ FLT_MIN = float(np.finfo(np.float32).tiny)
 class Problem(ctypes.Structure):
     _fields_ = [("I", c_int64), ("J", c_int64), ("M", c_int64),
                 ("x", c_void_p), ("a", c_void_p), ("Rp", c_void_p),
-                ("lambda0", c_void_p), ("rh0", c_void_p), ("ru0", c_void_p)]
+                ("lambda0", c_void_p), ("rh0", c_void_p), ("ru0", c_void_p),
+                ("b", c_void_p), ("rp_c64", c_int)]
 
 
 class Options(ctypes.Structure):
@@ -56,8 +59,9 @@ _LIB = None
 
 
 def header_symbols() -> List[str]:
-    """Names of every function the public header declares."""
-    src = open(HEADER).read()
+    """Names of every function the public headers (include/*.h) declare."""
+    import glob
+    src = "".join(open(h).read() for h in sorted(glob.glob(os.path.join(os.path.dirname(HEADER), "*.h"))))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(rcscm_[a-z_0-9]+)\s*\(", src)))
 
@@ -101,6 +105,7 @@ def lib():
         "rcscm_host_run": (c_int, [vp, vp, vp, vp, vp, vp, vp, c_int, vp, vp, vp, vp]),
         "rcscm_host_destroy": (None, [vp]),
         "rcscm_ilrma_init": (c_int, [POINTER(Ilrma), c_int, vp, vp]),
+        "rcscm_probe_fma": (c_int, [c_int, c_int, ctypes.c_longlong, vp, vp, POINTER(c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -125,7 +130,7 @@ def options(rule: str = "accel", alpha: float = 1.1, beta: float = 1e-16, ru_flo
             ckpt_stride: int = 0, ckpt_max_iters: int = 0) -> Options:
     o = Options()
     lib().rcscm_default_options(ctypes.byref(o))
-    o.rule = {"accel": RULE_ACCEL, "naive": RULE_NAIVE, "naive64": RULE_NAIVE_F64, "accel1": RULE_ACCEL1}[rule]
+    o.rule = RULES[rule]
     o.alpha, o.beta, o.ru_floor, o.null_tol = alpha, beta, ru_floor, null_tol
     o.block, o.iters_per_launch, o.persistent = block, iters_per_launch, int(persistent)
     o.ckpt_stride, o.ckpt_max_iters = int(ckpt_stride), int(ckpt_max_iters)
@@ -157,9 +162,10 @@ class Solver:
     """A context over one or more utterances held in CUDA tensors.
 
     Each problem is a dict with x (complex64 [I, J, M]), a (complex128 [I, M]),
-    Rp (complex128 [I, M, M]), rh0, ru0 (float32 [I, J]) and optionally lambda0
-    (float64 [I]).  The tensors must stay alive and unchanged while the Solver
-    exists (it keeps references to them).
+    Rp (complex128, or complex64, [I, M, M]), rh0, ru0 (float32 [I, J]) and
+    optionally lambda0 (float64 [I]) and b (complex128 [I, M], the caller's null
+    vector of R', validated by the setup).  The tensors must stay alive and
+    unchanged while the Solver exists (it keeps references to them).
     """
 
     def __init__(self, problems: Sequence[dict], rule: str = "accel", stream=None, **opts):
@@ -173,7 +179,11 @@ class Solver:
             q.I, q.J, q.M = I, J, M
             q.x = _dev(p["x"], torch.complex64, (I, J, M), "x")
             q.a = _dev(p["a"], torch.complex128, (I, M), "a")
-            q.Rp = _dev(p["Rp"], torch.complex128, (I, M, M), "Rp")
+            rp_c64 = p["Rp"].dtype == torch.complex64
+            q.Rp = _dev(p["Rp"], torch.complex64 if rp_c64 else torch.complex128, (I, M, M), "Rp")
+            q.rp_c64 = int(rp_c64)
+            b = p.get("b")
+            q.b = _dev(b, torch.complex128, (I, M), "b") if b is not None else None
             q.rh0 = _dev(p["rh0"], torch.float32, (I, J), "rh0")
             q.ru0 = _dev(p["ru0"], torch.float32, (I, J), "ru0")
             lam0 = p.get("lambda0")

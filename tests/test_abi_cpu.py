@@ -41,9 +41,11 @@ def test_header_is_plain_c_and_struct_layout_matches(tmp_path, L):
 #include <stdio.h>
 #include <stddef.h>
 #include "rcscm.h"
+#include "rcscm_probe.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(rcscm_problem), offsetof(rcscm_problem, x),
-         offsetof(rcscm_problem, ru0), sizeof(rcscm_options), offsetof(rcscm_options, iters_per_launch));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(rcscm_problem), offsetof(rcscm_problem, x),
+         offsetof(rcscm_problem, ru0), offsetof(rcscm_problem, b), offsetof(rcscm_problem, rp_c64),
+         sizeof(rcscm_options), offsetof(rcscm_options, iters_per_launch));
   return 0;
 }
 ''')
@@ -51,8 +53,8 @@ int main(void) {
     subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    want = [ctypes.sizeof(R.Problem), R.Problem.x.offset, R.Problem.ru0.offset,
-            ctypes.sizeof(R.Options), R.Options.iters_per_launch.offset]
+    want = [ctypes.sizeof(R.Problem), R.Problem.x.offset, R.Problem.ru0.offset, R.Problem.b.offset,
+            R.Problem.rp_c64.offset, ctypes.sizeof(R.Options), R.Options.iters_per_launch.offset]
     assert got == want
 
 

@@ -140,3 +140,18 @@ def test_sharded_batch_equals_unsharded():
         for i, out in zip(mine, part):
             for k in ("rh", "ru", "lam", "h"):
                 np.testing.assert_array_equal(out[k], whole[i][k])
+
+
+def test_frequency_ranges_equal_unsharded():
+    # one utterance split into the contiguous frequency ranges that two ranks would
+    # solve, run one after another on this GPU: bit for bit the rows of the whole
+    # utterance (rows are independent; every range runs the same kernel shape)
+    import bench
+    p = synth.make_problem(synth.ProblemSpec(M=4, I=37, J=1000, K=5, spacing=0.03), 950)
+    (whole,), _ = gpu_run([p], 12)
+    for rank in range(2):
+        i0, i1 = bench.freq_range(37, rank, 2)
+        (part,), st = gpu_run([bench.slice_rows(p, i0, i1)], 12)
+        assert st == 0
+        for k in ("rh", "ru", "lam", "h"):
+            np.testing.assert_array_equal(part[k], whole[k][i0:i1])
