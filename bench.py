@@ -84,6 +84,9 @@ def parse():
                     help="skip the section that times the initialisation from ILRMA outputs")
     ap.add_argument("--adjoint-workload", default="adjoint-16")
     ap.add_argument("--adjoint-steps", type=int, default=5)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload section")
+    ap.add_argument("--batch-utt", type=int, default=None,
+                    help="utterances of the batch section (default all 256 of batch-256)")
     return ap.parse_args()
 
 
@@ -215,6 +218,54 @@ def shard(weights, rank, ws):
         owner[i] = r
         load[r] += weights[i]
     return [i for i in range(len(weights)) if owner[i] == rank]
+
+
+def freq_range(I, rank, ws):
+    """Contiguous frequency rows [i0, i1) that rank `rank` of `ws` solves when one
+    utterance is split over the ranks: rows are independent in every rule, all rows of
+    an utterance have the same J, so equal row counts (within one) balance the work.
+    The ranges are disjoint and cover 0..I-1 in order."""
+    return I * rank // ws, I * (rank + 1) // ws
+
+
+def slice_rows(p, i0, i1):
+    """The rows [i0, i1) of a generator problem (every per-frequency input)."""
+    keys = ("x", "a", "Rp", "rh0", "ru0")
+    q = {k: np.ascontiguousarray(p[k][i0:i1]) for k in keys}
+    if p.get("lambda0") is not None:
+        q["lambda0"] = np.ascontiguousarray(p["lambda0"][i0:i1])
+    return q
+
+
+def fp32_peak(R, dev, stream, sampler=None, reps=5):
+    """Measured throughput of the FP32 FMA pipe (lane-ops/s): the library's probe
+    kernel (16 independent FMA chains per thread, 8 blocks of 256 threads per SM)
+    timed with CUDA events on the launching stream, best of `reps` launches, as
+    scalar FFMA and as packed f32x2 FMA."""
+    import ctypes
+
+    import torch
+    L = R.lib()
+    n_blocks = 8 * torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.zeros(n_blocks * 256, dtype=torch.float32, device=dev)
+    out = {}
+    for packed, name in ((0, "ffma"), (1, "ffma2")):
+        best = 0.0
+        for k in range(reps + 2):
+            ops = ctypes.c_double()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            code = L.rcscm_probe_fma(packed, n_blocks, 4000, ctypes.c_void_p(sink.data_ptr()),
+                                     ctypes.c_void_p(stream.cuda_stream), ctypes.byref(ops))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            assert code == R.OK, R.strerror(code)
+            if k >= 2:
+                best = max(best, ops.value / (e0.elapsed_time(e1) / 1e3))
+        out[name] = best / 1e9
+    return {"ffma_gops": out["ffma"], "ffma2_gops": out["ffma2"], "unit": "G lane-ops/s",
+            "how": f"rcscm_probe_fma: {n_blocks} blocks x 256 threads x 4000 rounds x 16 independent FMA lanes, "
+                   "best of 5 launches, CUDA events on the launching stream"}
 
 
 def make_inputs(name, n_utt=None):
@@ -353,6 +404,27 @@ def time_steps(solver, h, n_iter, K, W, flush, stream, sampler=None, preroll_s=0
     return one, names
 
 
+def solver_state(solver, n_probs):
+    """(r_h, r_u, lambda) of every utterance of a context, concatenated (device tensors)."""
+    import torch
+    parts = [solver.get_state(k) for k in range(n_probs)]
+    return [torch.cat([p[i].reshape(-1) for p in parts]) for i in range(3)]
+
+
+def state_agreement(a, b, ha, hb):
+    """Relative 2-norm differences of r_h, r_u, lambda and the SNR (dB) between the
+    Wiener outputs of two GPU rules run from the same initial state."""
+    import torch
+    out = {}
+    for name, u, v in zip(("rh", "ru", "lam"), a, b):
+        u, v = u.double(), v.double()
+        out[name] = float(torch.linalg.vector_norm(u - v) / torch.linalg.vector_norm(v))
+    ha, hb = torch.view_as_real(ha).double(), torch.view_as_real(hb).double()
+    err = float(torch.sum((ha - hb) ** 2))
+    out["sdr_db"] = float(10 * np.log10(float(torch.sum(hb ** 2)) / max(err, 1e-300)))
+    return out
+
+
 def fused_ops_per_launch(specs, n_iter):
     """FP32 lane-ops of one fused launch: per slot, 26 per pass, the projection
     Phi x (8M + (M-2)(4M+3) + 1) and the Wiener filter (12 + 4M)."""
@@ -382,8 +454,14 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     wl, probs = make_inputs(args.workload, args.n_utt)
     n_iter = wl.n_iter
-    sharded = ws > 1 and len(probs) > 1 and not args.replicate
-    if sharded:                          # each rank solves its share of the utterances (strong scaling)
+    sharded = ws > 1 and not args.replicate
+    split_rows = sharded and len(probs) == 1
+    if split_rows:                       # one utterance: each rank solves a contiguous range of frequency rows
+        import dataclasses
+        i0, i1 = freq_range(wl.specs[0].I, rank, ws)
+        probs = [slice_rows(probs[0], i0, i1)]
+        wl_specs = [dataclasses.replace(wl.specs[0], I=i1 - i0)]
+    elif sharded:                        # each rank solves its share of the utterances (strong scaling)
         mine = shard([sp.I * sp.J for sp in wl.specs], rank, ws)
         probs = [probs[i] for i in mine]
         wl_specs = [wl.specs[i] for i in mine]
@@ -463,16 +541,22 @@ def run_ours(args):
     iters_per_launch = n_iter if args.iters_per_launch == 0 else args.iters_per_launch
 
     clocks = sampler.summary() if sampler else None
+    probe = fp32_peak(R, dev, stream)
+    peak_derived = GB300_SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+    peak_measured = max(probe["ffma_gops"], probe["ffma2_gops"])
+    peak_src = (f"measured: FP32 FMA probe on this GPU ({probe['ffma_gops']:.0f} scalar FFMA, "
+                f"{probe['ffma2_gops']:.0f} packed f32x2 G lane-ops/s; the larger is the peak); derived "
+                f"152 SMs x 128 lanes x 2070 MHz = {peak_derived:.0f}")
     if fused and not args.graph:
         ops = fused_ops_per_launch(wl_specs, n_iter) * args.replicas
         achieved = ops / (launch_ms / 1e3) / 1e9
-        peak = GB300_SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+        peak = peak_measured
         traffic, tsrc = profiled_traffic("solve_kernel", f"{wl.name}-x{args.replicas}")
         m_bytes = sum(sp.I * sp.J * (16 * sp.M + 36) for sp in wl_specs) * args.replicas
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (FP32 lane-ops)",
                     "frac": achieved / peak, "traffic": traffic, "traffic_source": tsrc,
-                    "traffic_algorithmic": m_bytes,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz max SM clock",
+                    "traffic_algorithmic": m_bytes, "frac_of_derived": achieved / peak_derived,
+                    "peak_source": peak_src, "fp32_probe": probe,
                     "kernel": "solve_kernel (invariants from x, all passes in registers, Wiener output; one launch)",
                     "algorithmic": (f"{ACCEL_FP32_OPS_PER_SLOT_ITER} FP32 ops + 2 MUFU per slot-pass, plus the "
                                     "projection and the Wiener filter once per slot (f32x2 counts 2)"),
@@ -480,12 +564,12 @@ def run_ours(args):
     elif args.rule == "accel" and args.iters_per_launch == 0:
         ops = ACCEL_FP32_OPS_PER_SLOT_ITER * slots * iters_per_launch
         achieved = ops / (launch_ms / 1e3) / 1e9
-        peak = GB300_SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+        peak = peak_measured
         traffic, tsrc = profiled_traffic("accel_kernel", f"{wl.name}-x{args.replicas}-resident")
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (FP32 lane-ops)",
                     "frac": achieved / peak, "traffic": traffic, "traffic_source": tsrc,
                     "traffic_algorithmic": ACCEL_BYTES_PER_SLOT_LAUNCH * slots,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz max SM clock",
+                    "frac_of_derived": achieved / peak_derived, "peak_source": peak_src, "fp32_probe": probe,
                     "kernel": "accel_kernel (register-resident, all iterations in one launch)",
                     "algorithmic": f"{ACCEL_FP32_OPS_PER_SLOT_ITER} FP32 ops + 2 MUFU per slot-iteration (f32x2 counts 2)",
                     "hbm_gbs_algorithmic": ACCEL_BYTES_PER_SLOT_LAUNCH * slots / (launch_ms / 1e3) / 1e9}
@@ -520,7 +604,9 @@ def run_ours(args):
                    "path": "fused (rcscm_setup_freq + rcscm_run)" if fused else "separate (setup, iterate, extract)",
                    "step": "setup + invariants + n_iter EM passes + Wiener extraction, inputs resident in HBM",
                    "l2": "flushed between timed steps (256 MB write outside the step's event brackets)",
-                   "parallelism": (f"utterances sharded over {ws} GPUs (LPT by I*J), no data-path collective"
+                   "parallelism": (f"frequency rows split into {ws} contiguous ranges, one per GPU, no data-path "
+                                   "collective" if split_rows else
+                                   f"utterances sharded over {ws} GPUs (LPT by I*J), no data-path collective"
                                    if sharded else f"replicas x{ws} (the whole workload per GPU, no collective)")},
         "kernels_ms": ({k: statistics.mean(v) for k, v in seg.items()} if not args.graph
                        else {"step_graph": ms_per_step, "iterate_alone": it_ms}),
@@ -533,53 +619,70 @@ def run_ours(args):
     }
 
     # ---------------- naive rule on the same workload (accel vs naive at M=4)
-    if not args.no_naive and args.rule == "accel":
+    if not args.no_naive and args.rule == "accel" and ws == 1:
         kn = args.naive_steps if args.naive_steps is not None else min(args.steps, 10)
+        acc_state = solver_state(solver, len(dprobs))
+        acc_h = h.clone()
+        names = {"accel1": "first-stage (Algorithm 1)",
+                 "naive": "naive (per-slot explicit inverse, whitened coordinates of R~_i), FP32",
+                 "naive_printed": "naive (per-slot explicit inverse, printed coordinates), FP32",
+                 "naive64": "naive (per-slot explicit inverse, printed coordinates), FP64"}
         for key, rule, k_steps in (("first_stage", "accel1", kn), ("naive", "naive", kn),
-                                   ("naive_f64", "naive64", max(1, min(kn, 3)))):
+                                   ("naive_printed", "naive_printed", kn), ("naive_f64", "naive64", max(1, min(kn, 3)))):
             nsolver = R.Solver(dprobs, rule=rule)
             none, _ = time_steps(nsolver, h, n_iter, k_steps, 1, flush, stream)
-            barrier()
             torch.cuda.synchronize()
             nev = [none(True) for _ in range(k_steps)]
             torch.cuda.synchronize()
             ncode = nsolver.status()
             n_ms = statistics.mean(e[0].elapsed_time(e[3]) for e in nev)
             n_it = statistics.mean(e[1].elapsed_time(e[2]) for e in nev)
+            agree = state_agreement(solver_state(nsolver, len(dprobs)), acc_state, h, acc_h)
             nsolver.close()
             result[key] = {"value": slots * n_iter / (n_ms / 1e3), "ms_per_step": n_ms, "iterate_ms": n_it,
                            "steps": k_steps, "arithmetic": "f64" if rule == "naive64" else "f32",
-                           "rule": {"accel1": "first-stage (Algorithm 1)", "naive": "naive (per-slot inverse)",
-                                    "naive64": "naive, FP64"}[rule],
-                           "status": R.strerror(ncode),
+                           "rule": names[rule], "status": R.strerror(ncode),
                            "speedup_second_stage_step": n_ms / ms_per_step,
-                           "speedup_second_stage_iterate": n_it / it_ms}
+                           "speedup_second_stage_iterate": n_it / it_ms,
+                           "agreement_with_second_stage": agree}
         result["naive"]["paper"] = ("87x: second-stage vs naive per iteration, MATLAB R2019a FP64 on an "
                                     "Intel Core i9-7900X, M=4, I=513, J~275")
+        result["naive"]["accuracy"] = (
+            "against the FP64 oracle (tests/test_gpu_parity.py): the FP32 naive rule meets 1e-5 after one pass, "
+            "1e-3 and 60 dB after full runs, including the 100-pass single-m4 rows; the printed-coordinates FP32 "
+            "form does not (1e-4 to 1e-2 after one pass) and is timed for reference only")
 
     # ---------------- streaming mode: one pass per launch over a working set larger than L2
-    if not args.no_streaming and args.rule == "accel":
+    if not args.no_streaming and args.rule == "accel" and ws == 1:
         same = args.streaming_workload == args.workload and args.replicas == 1
         result["streaming"] = streaming_roofline(args, R, dev, peaks, stream, reuse=(wl, dprobs) if same else None)
 
     # ---------------- adjoint (forward with checkpoints + rcscm_backward)
-    if not args.no_adjoint and args.rule == "accel":
+    if not args.no_adjoint and args.rule == "accel" and ws == 1:
         result["adjoint"] = adjoint_section(args, R, dev, stream)
 
     # ---------------- estimator inputs from the ILRMA stage's outputs (rcscm_ilrma_init)
-    if not args.no_ilrma and args.replicas == 1:
+    if not args.no_ilrma and args.replicas == 1 and ws == 1:
         result["ilrma_init"] = ilrma_section(probs, R, dev, peaks, flush, stream, wl.name)
+
+    # ---------------- the batched workload (many utterances, mixed M, uneven J)
+    if not args.no_batch and args.rule == "accel" and ws == 1 and args.workload != "batch-256":
+        result["batch"] = batch_section(args, R, dev, peaks, flush, stream)
 
     # ---------------- end to end through the C ABI with host buffers
     if not args.no_e2e and len(probs) == 1 and args.replicas == 1:
+        barrier()
         piped = e2e_host(probs[0], n_iter, args, R, n_chunks=args.e2e_chunks)
-        zc = e2e_zero_copy(probs[0], n_iter, args, R) if args.rule == "accel" else None
+        if ws > 1:                        # whole job: all ranks' slots over the slowest rank's step
+            piped = combine_ranks(piped, probs[0]["x"].shape[0] * probs[0]["x"].shape[1], n_iter, dev)
+        zc = e2e_zero_copy(probs[0], n_iter, args, R) if args.rule == "accel" and ws == 1 else None
         best = zc if zc is not None and zc["value"] > piped["value"] else piped
         result["e2e"] = best
         result["e2e_pipelined"] = piped
         if zc is not None:
             result["e2e_zero_copy"] = zc
-        result["e2e_oneshot"] = e2e_oneshot(probs[0], n_iter, args, R)
+        if ws == 1:
+            result["e2e_oneshot"] = e2e_oneshot(probs[0], n_iter, args, R)
     elif not args.no_e2e:
         result["e2e"] = None
 
@@ -588,6 +691,94 @@ def run_ours(args):
         result["cpu_baseline"] = cpu_baseline(probs[0], wl, args.rule)
     solver.close()
     return result if rank == 0 else None
+
+
+def combine_ranks(res, slots, n_iter, dev):
+    """Whole-job form of a per-rank end-to-end result: the slots of every rank over
+    the slowest rank's step time (host-side bookkeeping, outside the timed region)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([res["ms_per_step"], float(slots), float(res["h2d_bytes_per_step"]),
+                      float(res["d2h_bytes_per_step"])], dtype=torch.float64, device=dev)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    out = dict(res)
+    out.update(ms_per_step=float(mx[0]), value=float(t[1]) * n_iter / (float(mx[0]) / 1e3),
+               h2d_bytes_per_step=int(t[2]), d2h_bytes_per_step=int(t[3]))
+    out["api"] = res["api"] + ", every rank on its own frequency rows; slowest rank's step"
+    return out
+
+
+def batch_section(args, R, dev, peaks, flush, stream):
+    """The batched workload: many utterances with uneven J and mixed M in one
+    context.  (1) The whole step -- setup, n_iter passes with the row resident,
+    Wiener output -- with the launch shape picked by rcscm_autotune and the step
+    replayed as a CUDA graph, L2 flushed between steps.  (2) The accelerated kernel
+    one pass per launch (state streamed through HBM) against the measured HBM peak:
+    36 algorithmic bytes per slot per launch."""
+    import torch
+    wl, probs = make_inputs("batch-256", args.batch_utt)
+    n_iter = wl.n_iter
+    dprobs = [R.to_device(p, dev) for p in probs]
+    del probs
+    out = {"workload": f"batch-256: {len(dprobs)} utterances, I=513, J in [200, 2000], M in {{2, 4, 6}}",
+           "n_iter": n_iter}
+    s = R.Solver(dprobs, rule="accel")
+    slots = s.info()["slots"]
+    h = torch.empty(s.out_elements, dtype=torch.complex64, device=dev)
+    s.setup()
+    block, persistent = s.autotune(n_iter_probe=min(n_iter, 10))
+    s.graph_create(n_iter, h)
+    for _ in range(3):
+        s.graph_launch()
+    torch.cuda.synchronize()
+    k = max(3, min(args.steps, 10))
+    ms = []
+    for _ in range(k):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.graph_launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    code = s.status()
+    s.close()
+    t = statistics.mean(ms)
+    out["resident"] = {"value": slots * n_iter / (t / 1e3), "unit": UNIT, "ms_per_step": t, "steps": k,
+                       "slots": slots, "status": R.strerror(code),
+                       "shape": {"block": block, "persistent": persistent, "autotuned": True,
+                                 "cuda_graph": True},
+                       "step": "setup + invariants + n_iter passes + Wiener, one graph replay, L2 flushed between"}
+    s = R.Solver(dprobs, rule="accel", iters_per_launch=1)
+    s.setup()
+    shape = s.autotune(n_iter_probe=1)
+    for _ in range(3):
+        s.iterate(1)
+    n = max(10, min(args.streaming_launches, 30))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for j in range(n):
+        s.iterate(1)
+        ev[j + 1].record(stream)
+    torch.cuda.synchronize()
+    code = s.status()
+    s.close()
+    tl = statistics.median(ev[j].elapsed_time(ev[j + 1]) for j in range(n))
+    bytes_ = ACCEL_BYTES_PER_SLOT_LAUNCH * slots
+    achieved = bytes_ / (tl / 1e3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic, tsrc = profiled_traffic("accel_stream_kernel", "batch-256-streaming")
+    out["streaming"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": traffic, "traffic_source": tsrc, "traffic_algorithmic": bytes_,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured burst copy)" if peaks
+                        else "fallback 6800 GB/s",
+                        "launch_us_median": 1e3 * tl, "launches": n, "slot_updates_per_s": slots / (tl / 1e3),
+                        "shape": {"block": shape[0], "persistent": shape[1], "autotuned": True},
+                        "status": R.strerror(code)}
+    return out
 
 
 def streaming_roofline(args, R, dev, peaks, stream, reuse=None):
