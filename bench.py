@@ -173,7 +173,8 @@ KERNEL_SOURCES = {
     "naive_kernel": ["naive.cu", "rcscm_internal.cuh"],
     "adjoint_kernel": ["accel_common.cuh", "adjoint.cu", "rcscm_internal.cuh"],
     "ilrma_init_kernel": ["ilrma.cu", "ilrma.cuh", "rcscm_internal.cuh"],
-    "accel1_kernel": ["accel1.cu", "accel_common.cuh", "rcscm_internal.cuh"],
+    "accel1_kernel": ["accel1.cu", "accel_common.cuh", "dfloat.cuh", "rcscm_internal.cuh"],
+    "naive_white_kernel": ["naive.cu", "rcscm_internal.cuh"],
     "invariants_kernel": ["setup.cu", "rcscm_internal.cuh"],
     "extract_kernel": ["extract.cu", "rcscm_internal.cuh"],
 }

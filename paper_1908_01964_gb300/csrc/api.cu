@@ -433,7 +433,7 @@ int rcscm_iterate(rcscm_ctx* c, int n_iter, void* stream) {
         if (c->opt.rule == RCSCM_RULE_ACCEL)
             e = launch_accel(c->d, (int)c->R, c->max_j, c->opt.block, k, pk, c->opt.persistent != 0, cs);
         else if (c->opt.rule == RCSCM_RULE_ACCEL1)
-            e = launch_accel1(c->d, (int)c->R, c->max_j, k, p, cs);
+            e = launch_accel1(c->d, c->naive_rows, c->count_by_m, c->first_by_m, c->max_j, k, p, cs);
         else
             e = launch_naive(c->d, c->naive_rows, c->count_by_m, c->first_by_m, k, p, c->opt.rule, cs);
         if (e != cudaSuccess) return map_cuda(e);

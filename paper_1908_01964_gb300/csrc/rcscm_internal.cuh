@@ -339,8 +339,9 @@ cudaError_t launch_naive(const DevState& d, const int* rows_by_m, const int* cou
 cudaError_t launch_extract(const DevState& d, int n_blocks, float2* h_out, cudaStream_t s);
 // First-stage rule (accel1.cu): threads per row for rows of up to max_j frames (0: too long).
 int accel1_block(int max_j);
-cudaError_t launch_accel1(const DevState& d, int n_rows, int max_j, int n_iter, const IterParams& p,
-                          cudaStream_t s);
+// rows_by_m / count_by_m / first_by_m as for launch_naive.
+cudaError_t launch_accel1(const DevState& d, const int* rows_by_m, const int* count_by_m, const int* first_by_m,
+                          int max_j, int n_iter, const IterParams& p, cudaStream_t s);
 cudaError_t launch_adjoint(const DevState& d, int n_rows, int max_j, int block, const AdjointArgs& a,
                            const IterParams& p, cudaStream_t s);
 }  // namespace rcscm
