@@ -238,3 +238,78 @@ def _make_full(args):
 def tiny(M: int = 3, I: int = 5, J: int = 7, K: int = 3, seed: int = 7, **kw) -> dict:
     """A tiny problem for brute-force checks."""
     return make_problem(ProblemSpec(M=M, I=I, J=J, K=K, **kw), seed)
+
+
+# --------------------------------------------------------------------------
+# Inputs of the front end (STFT and ILRMA).  Random draws and signal synthesis
+# only: no STFT, no ILRMA update and no estimator arithmetic.
+# --------------------------------------------------------------------------
+
+def ilrma_init_values(I: int, J: int, N: int, K: int, seed: int):
+    """Non-negative random initial NMF variables of ILRMA (Sec. IV-A: "initialized by
+    nonnegative random values"): T0 [N, I, K], V0 [N, K, J], uniform in [0.1, 1.1)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    T0 = rng.uniform(0.1, 1.1, size=(N, I, K))
+    V0 = rng.uniform(0.1, 1.1, size=(N, K, J))
+    return T0, V0
+
+
+def make_bss_mixture(M: int, I: int, J: int, K: int, seed: int) -> dict:
+    """A determined, noise-free instantaneous mixture per frequency: x_ij = A_i s_ij with
+    M sources whose variances are rank-K NMF products (Gamma(1, 1) bases and
+    activations, one set per source) and a random mixing matrix A_i (complex Gaussian
+    entries, each column scaled to unit norm).  Returns x (complex64 [I, J, M]), A
+    (complex128 [I, M, M]), s (complex128 [I, J, M]) and ILRMA's initial T0, V0."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Tn = rng.gamma(1.0, 1.0, size=(M, I, K))
+    Vn = rng.gamma(1.0, 1.0, size=(M, K, J)) ** 2          # sparse-ish activations
+    r = np.einsum("nik,nkj->ijn", Tn, Vn)
+    s = np.sqrt(r / 2.0) * (rng.standard_normal((I, J, M)) + 1j * rng.standard_normal((I, J, M)))
+    A = rng.standard_normal((I, M, M)) + 1j * rng.standard_normal((I, M, M))
+    A /= np.linalg.norm(A, axis=1, keepdims=True)
+    x = np.einsum("imn,ijn->ijm", A, s).astype(np.complex64)
+    T0, V0 = ilrma_init_values(I, J, M, K, seed + 1)
+    return dict(x=x, A=A, s=s, T0=T0, V0=V0)
+
+
+def make_time_mixture(M: int, n_samples: int, seed: int, spacing: float = 0.04, snr_db: float = 0.0,
+                      target_deg: float = 30.0, n_noise: int = 19) -> dict:
+    """Multichannel time-domain mixture at fs = 16 kHz in the paper's arrangement
+    (Sec. IV-A): a directional target 30 degrees from the array normal and a diffuse
+    babble stand-in made of n_noise independent sources at 10-degree intervals, mixed
+    at the given speech-to-noise ratio, on a linear array.  Each source signal is
+    white noise shaped by a random two-pole resonance and a slowly varying random
+    envelope (a speech-like, non-stationary spectrum); propagation to each microphone
+    is a plane-wave delay applied as a phase shift of the source's whole-signal
+    spectrum.  Returns sig (float64 [M, n_samples]), target (the target's image at the
+    microphones, float64 [M, n_samples]) and the target direction."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xs = (np.arange(M) - (M - 1) / 2.0) * spacing
+    n = n_samples
+    freqs = np.fft.rfftfreq(n, d=1.0 / FS)
+
+    def source():
+        e = rng.standard_normal(n + 2)
+        f0 = rng.uniform(200.0, 3000.0)
+        rho = rng.uniform(0.85, 0.98)
+        a1, a2 = 2.0 * rho * np.cos(2.0 * np.pi * f0 / FS), -rho * rho
+        y = np.zeros(n + 2)
+        for t in range(2, n + 2):
+            y[t] = e[t] + a1 * y[t - 1] + a2 * y[t - 2]
+        env = np.repeat(rng.gamma(1.0, 1.0, size=n // 800 + 2), 800)[:n]
+        kern = np.hanning(801)
+        env = np.convolve(env, kern / kern.sum(), mode="same")
+        sig = y[2:] * env
+        return sig / np.sqrt(np.mean(sig ** 2))
+
+    def image(sig, deg):
+        th = np.deg2rad(deg)
+        delay = xs * np.sin(th) / C_SOUND                     # [M] seconds
+        S = np.fft.rfft(sig)
+        return np.fft.irfft(S[None, :] * np.exp(-2j * np.pi * freqs[None, :] * delay[:, None]), n=n, axis=1)
+
+    target = image(source(), target_deg)
+    angles = -90.0 + 10.0 * np.arange(n_noise)
+    noise = sum(image(source(), d) for d in angles)
+    g = np.sqrt(np.mean(target ** 2) / np.mean(noise ** 2) / 10.0 ** (snr_db / 10.0))
+    return dict(sig=target + g * noise, target=target, target_deg=target_deg, spacing=spacing)
