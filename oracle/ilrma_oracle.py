@@ -117,7 +117,9 @@ def cost(Xs, W, T, V):
 
 # Floor of the NMF variables after each update: where the separation is exact some
 # |y|^2 vanish and the multiplicative updates would drive t, v (and so r) to zero.
-NMF_FLOOR = 1e-10
+# With the scale normalisation keeping the mean output power at 1, t, v >= 1e-6 keeps
+# r >= 1e-12 and 1 / r^2 within the range of single precision.
+NMF_FLOOR = 1e-6
 
 
 def update_T(P, T, V, n):

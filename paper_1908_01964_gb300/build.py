@@ -24,7 +24,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "librcscm.so")
 LIB_DEBUG = os.path.join(PKG, "librcscm_debug.so")
-SOURCES = ["api.cu", "setup.cu", "iterate.cu", "naive.cu", "extract.cu", "objective.cu", "host.cu", "noalloc.cu", "adjoint.cu", "accel1.cu", "ilrma.cu", "probe.cu"]
+SOURCES = ["api.cu", "setup.cu", "iterate.cu", "naive.cu", "extract.cu", "objective.cu", "host.cu", "noalloc.cu", "adjoint.cu", "accel1.cu", "ilrma.cu", "probe.cu", "frontend.cu"]
 # (threads per row, slots per thread) shapes of the accelerated kernels: iterate_inst.cu
 # is compiled once per shape so that the large unrolled kernels build in parallel.
 INSTANCES = [(32, 4), (32, 8), (64, 4), (64, 8), (128, 4), (128, 8), (256, 4), (256, 8), (512, 4), (512, 8),

@@ -310,6 +310,7 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
         ej[t] = e < MM ? e - (e / M) * M : 0;
     }
     bool done = false;                  // this group's refinement has converged
+    bool clustered = false;             // its last step treated some pair as a cluster
     for (int step = 0; step < kRefineMaxSteps; ++step) {
         double2 rv[NE], sv[NE];
 #pragma unroll
@@ -350,7 +351,7 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
         rr2 = group_sum_f(rr2);
         const float delta = 2.f * (sqrtf(so2) + afro * sqrtf(rr2));
         __syncwarp();
-        float emax = 0.f;
+        float emax = 0.f, clus = 0.f;
 #pragma unroll
         for (int t = 0; t < NE; ++t) {                     // E (FP32)
             const int e = l + kGroupLanes * t;
@@ -364,12 +365,15 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
                     const float dl = (float)(lj - slam[g][i]);
                     ee = fabsf(dl) > delta ? cscale(to_f2(zadd(sv[t], zscale(rv[t], lj))), 1.f / dl)
                                            : cscale(to_f2(rv[t]), 0.5f);
+                    clus = fabsf(dl) > delta ? clus : 1.f;
                 }
                 E32[i][j] = ee;
                 emax = fmaxf(emax, cabs2(ee));
             }
         }
         emax = group_max_f(emax);
+        clus = group_max_f(clus);
+        if (!done) clustered = clus > 0.f;                 // this group's last step treated a cluster
         __syncwarp();
 #pragma unroll
         for (int t = 0; t < NE; ++t) {                     // X <- X + X E
@@ -388,6 +392,98 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
         // group leaves X and lambda alone while the other group of its warp continues.
         done = done || !(emax > 1e-12f);
         if (__all_sync(0xffffffffu, done)) break;
+    }
+
+    // ---- phase 3: exact rotations inside clusters (FP64) ---------------------------
+    // The refinement's correction (S_ij + lambda_j R_ij) / (lambda_j - lambda_i) is a
+    // first-order step, taken only for pairs whose eigenvalues are further apart than its
+    // threshold delta; for closer pairs (a cluster) it restores orthogonality alone.  A
+    // rotation inside such a pair that the FP32 Jacobi could not resolve -- two small
+    // eigenvalues of R' a few FP32 units of |R'| apart, as ILRMA's noise estimate gives
+    // at low frequencies, where the null vector b and the 1/mu_2 term of (R')^+ depend on
+    // it -- is therefore never undone.  Here S = X^H R' X is formed again in FP64, and every
+    // pair whose eigenvector angle |S_pq| / |S_pp - S_qq| is still above 1e-9 (a converged
+    // pair sits near 1e-12, an unresolved cluster at 1e-7 to 1e-1) gets the exact 2 x 2
+    // Jacobi rotation (applied to S and X) by lane 0 of its group, and the eigenvalues are
+    // the Rayleigh quotients S_kk / |x_k|^2; rows without such a pair skip it.
+    {
+        // only rows whose refinement did not converge or ended with a cluster take part
+        const bool redo = active && (clustered || !done);
+#pragma unroll
+        for (int t = 0; t < NE; ++t) {                     // T = R' X
+            const int e = l + kGroupLanes * t;
+            if (redo && e < MM) {
+                const int i = ei[t], j = ej[t];
+                double2 tt = make_double2(0.0, 0.0);
+                for (int m = 0; m < M; ++m) tt = zfma(tt, A[i][m], X[m][j]);
+                T[i][j] = tt;
+            }
+        }
+        __syncwarp();
+        double2 sv[NE];
+#pragma unroll
+        for (int t = 0; t < NE; ++t) {                     // S = X^H T
+            const int e = l + kGroupLanes * t;
+            sv[t] = make_double2(0.0, 0.0);
+            if (redo && e < MM) {
+                const int i = ei[t], j = ej[t];
+                for (int m = 0; m < M; ++m) sv[t] = zfma_c(sv[t], X[m][i], T[m][j]);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < NE; ++t)
+            if (redo && l + kGroupLanes * t < MM) T[ei[t]][ej[t]] = sv[t];     // T now holds S
+        __syncwarp();
+        float couple = 0.f;
+#pragma unroll
+        for (int t = 0; t < NE; ++t) {
+            const int e = l + kGroupLanes * t;
+            if (redo && e < MM && ei[t] != ej[t]) {
+                const float gap = (float)(T[ei[t]][ei[t]].x - T[ej[t]][ej[t]].x);
+                const float off2 = cabs2(to_f2(sv[t]));
+                couple = fmaxf(couple, off2 > 1e-18f * gap * gap ? 1.f : 0.f);
+            }
+        }
+        couple = group_max_f(couple);
+        if (redo && couple > 0.f && l == 0) {
+            for (int p = 0; p < M - 1; ++p)
+                for (int q = p + 1; q < M; ++q) {
+                    const double g2 = zabs2(T[p][q]);
+                    const double gap = T[q][q].x - T[p][p].x;
+                    if (!(g2 > 1e-18 * gap * gap) || !(g2 > 0.0)) continue;
+                    const double gm = sqrt(g2);
+                    const double2 ep = make_double2(T[p][q].x / gm, T[p][q].y / gm);   // e^{i phi}
+                    const double2 ec = zconj(ep);
+                    const double tau = gap / (2.0 * gm);
+                    const double tn = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                    const double c = 1.0 / sqrt(1.0 + tn * tn), sn = tn * c;
+                    for (int k = 0; k < M; ++k) {         // columns of S and X: S G, X G
+                        const double2 sp = T[k][p], sq = zmul(ec, T[k][q]);
+                        T[k][p] = make_double2(c * sp.x - sn * sq.x, c * sp.y - sn * sq.y);
+                        T[k][q] = make_double2(sn * sp.x + c * sq.x, sn * sp.y + c * sq.y);
+                        const double2 xp = X[k][p], xq = zmul(ec, X[k][q]);
+                        X[k][p] = make_double2(c * xp.x - sn * xq.x, c * xp.y - sn * xq.y);
+                        X[k][q] = make_double2(sn * xp.x + c * xq.x, sn * xp.y + c * xq.y);
+                    }
+                    for (int k = 0; k < M; ++k) {         // rows of S: G^H S
+                        const double2 rp = T[p][k], rq = zmul(ep, T[q][k]);
+                        T[p][k] = make_double2(c * rp.x - sn * rq.x, c * rp.y - sn * rq.y);
+                        T[q][k] = make_double2(sn * rp.x + c * rq.x, sn * rp.y + c * rq.y);
+                    }
+                    T[p][q] = make_double2(0.0, 0.0);
+                    T[q][p] = make_double2(0.0, 0.0);
+                }
+        }
+        __syncwarp();
+        if (redo && l < M) {                         // unit columns, Rayleigh quotients
+            double n2 = 0.0;
+            for (int m = 0; m < M; ++m) n2 += zabs2(X[m][l]);
+            slam[g][l] = T[l][l].x / n2;
+            const double rn = rsqrt(n2);
+            for (int m = 0; m < M; ++m) X[m][l] = zscale(X[m][l], rn);
+        }
+        __syncwarp();
     }
 
     // ---- ascending order of the eigenvalues (ranks) --------------------------------

@@ -106,6 +106,12 @@ def lib():
         "rcscm_host_destroy": (None, [vp]),
         "rcscm_ilrma_init": (c_int, [POINTER(Ilrma), c_int, vp, vp]),
         "rcscm_probe_fma": (c_int, [c_int, c_int, ctypes.c_longlong, vp, vp, POINTER(c_double)]),
+        "rcscm_front_create": (c_int, [POINTER(vp), c_int64, c_int64, c_int, c_int, c_int]),
+        "rcscm_front_shape": (c_int, [vp, i64p, i64p]),
+        "rcscm_front_destroy": (None, [vp]),
+        "rcscm_front_stft": (c_int, [vp, vp, vp, vp]),
+        "rcscm_front_istft": (c_int, [vp, vp, vp, vp]),
+        "rcscm_front_ilrma": (c_int, [vp, vp, vp, vp, c_int, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -518,3 +524,70 @@ def solve_host(x, a, Rp, rh0, ru0, n_iter: int, lambda0=None, want_state: bool =
                                   ctypes.byref(o), int(n_iter), ptr(h), ptr(rh), ptr(ru), ptr(lam))
     _check(code, "rcscm_solve_host", allow=(OK, ECLAMP))
     return dict(h=h, rh=rh, ru=ru, lam=lam)
+
+
+class Front:
+    """rcscm_front_*: STFT, ILRMA and inverse STFT for signals of one shape (the front
+    end of the estimator; include/rcscm_frontend.h).  Tensors are CUDA tensors."""
+
+    def __init__(self, M: int, n_samples: int, n_fft: int = 1024, shift: int = 512, K: int = 10):
+        h = c_void_p()
+        _check(lib().rcscm_front_create(ctypes.byref(h), M, n_samples, n_fft, shift, K), "rcscm_front_create")
+        self.h = h
+        self.M, self.n_samples, self.n_fft, self.shift, self.K = M, n_samples, n_fft, shift, K
+        I, J = c_int64(), c_int64()
+        _check(lib().rcscm_front_shape(h, ctypes.byref(I), ctypes.byref(J)), "rcscm_front_shape")
+        self.I, self.J = I.value, J.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().rcscm_front_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def stft(self, sig, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.I, self.J, self.M), dtype=torch.complex64, device=sig.device)
+        _check(lib().rcscm_front_stft(self.h, _dev(sig, torch.float32, (self.M, self.n_samples), "sig"),
+                                      _dev(out, torch.complex64, (self.I, self.J, self.M), "X"), _stream(stream)),
+               "rcscm_front_stft")
+        return out
+
+    def istft(self, X, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.M, self.n_samples), dtype=torch.float32, device=X.device)
+        _check(lib().rcscm_front_istft(self.h, _dev(X, torch.complex64, (self.I, self.J, self.M), "X"),
+                                       _dev(out, torch.float32, (self.M, self.n_samples), "out"), _stream(stream)),
+               "rcscm_front_istft")
+        return out
+
+    def ilrma(self, X, T0, V0, n_iter: int, status=None, stream=None):
+        """Returns (W complex128 [I, M, M] for X itself, T float32 [N, I, K], V float32 [N, K, J])."""
+        import torch
+        dev = X.device
+        N, I, J, K = self.M, self.I, self.J, self.K
+        W = torch.empty((I, N, N), dtype=torch.complex128, device=dev)
+        T = torch.empty((N, I, K), dtype=torch.float32, device=dev)
+        V = torch.empty((N, K, J), dtype=torch.float32, device=dev)
+        st = status if status is not None else None
+        _check(lib().rcscm_front_ilrma(self.h, _dev(X, torch.complex64, (I, J, N), "X"),
+                                       _dev(T0, torch.float32, (N, I, K), "T0"),
+                                       _dev(V0, torch.float32, (N, K, J), "V0"), int(n_iter),
+                                       _dev(W, torch.complex128, (I, N, N), "W"), _dev(T, torch.float32, (N, I, K), "T"),
+                                       _dev(V, torch.float32, (N, K, J), "V"),
+                                       _dev(st, torch.int32, (1,), "status") if st is not None else None,
+                                       _stream(stream)), "rcscm_front_ilrma")
+        return W, T, V

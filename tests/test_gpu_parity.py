@@ -46,6 +46,42 @@ def test_setup_matches_oracle(M):
     np.testing.assert_allclose(g["sigma_ab"], np.einsum("im,im->i", np.conj(p["a"]), g["b"]), atol=1e-12)
 
 
+@pytest.mark.parametrize("M,ratio", [(2, 1e-7), (4, 1e-6), (4, 2e-7), (6, 5e-7), (8, 1e-7)])
+def test_setup_resolves_close_small_eigenvalues(M, ratio):
+    """R' whose two smallest eigenvalues (the null one and mu_2) are ratio * |R'| apart, as
+    ILRMA's noise estimate gives at low frequencies: a few FP32 units of |R'|, below what
+    the FP32 Jacobi resolves; the setup must still return the FP64 null vector and the
+    estimator the oracle's result."""
+    from paper_1908_01964_gb300 import rcscm as R
+    p = _tiny(M, I=6, J=200, seed=90 + M)
+    rng = np.random.default_rng(M)
+    I = p["x"].shape[0]
+    Rp = np.empty((I, M, M), np.complex128)
+    for i in range(I):
+        Z = rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M))
+        E, _ = np.linalg.qr(Z)
+        mu = np.concatenate([[0.0, ratio * (1 + i)], np.sort(rng.uniform(0.2, 1.0, M - 2))])
+        Rp[i] = (E * mu) @ np.conj(E.T)
+    p["Rp"] = 0.5 * (Rp + np.conj(np.transpose(Rp, (0, 2, 1))))
+    st = O.setup(p["a"], p["Rp"])
+    with R.Solver([R.to_device(p)]) as s:
+        s.setup()
+        g = {k: v.cpu().numpy() for k, v in s.get_setup(0).items()}
+        assert s.status() == R.OK
+    overlap = np.abs(np.einsum("im,im->i", np.conj(g["b"]), st.b))
+    report("setup_close_eigenvalues", M=M, ratio=ratio, b_angle=float(np.max(1 - overlap)),
+           tau_aa=float(np.max(np.abs(g["tau_aa"] / st.tau_aa - 1))))
+    np.testing.assert_allclose(overlap, 1.0, atol=1e-10)
+    # lambda_0 = mu_2 is ratio * |R'|: its attainable absolute accuracy is a small multiple of
+    # the FP64 rounding of |R'| (the largest eigenvalue), not of mu_2 itself
+    assert np.max(np.abs(g["lambda0"] - st.lam0) / st.mu[:, -1]) < 1e-10
+    np.testing.assert_allclose(g["tau_aa"], st.tau_aa, rtol=1e-8)
+    (o,), code = gpu_run([p], 3)
+    e = compare(o, oracle_run(p, 3))
+    report("solve_close_eigenvalues", M=M, ratio=ratio, gpu=e)
+    assert code == 0 and norm_max(e) < 1e-4 and e["sdr"] > SDR_MIN_DB, e
+
+
 def test_setup_uses_given_lambda0():
     from paper_1908_01964_gb300 import rcscm as R
     p = _tiny(4)
