@@ -85,6 +85,7 @@ def parse():
     ap.add_argument("--adjoint-workload", default="adjoint-16")
     ap.add_argument("--adjoint-steps", type=int, default=5)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload section")
+    ap.add_argument("--no-front", action="store_true", help="skip the front-end (STFT, ILRMA, iSTFT) section")
     ap.add_argument("--batch-utt", type=int, default=None,
                     help="utterances of the batch section (default all 256 of batch-256)")
     return ap.parse_args()
@@ -666,6 +667,10 @@ def run_ours(args):
     if not args.no_ilrma and args.replicas == 1 and ws == 1:
         result["ilrma_init"] = ilrma_section(probs, R, dev, peaks, flush, stream, wl.name)
 
+    # ---------------- the front end: STFT, ILRMA, inverse STFT (the paper's settings)
+    if not args.no_front and args.rule == "accel" and ws == 1:
+        result["front_end"] = front_section(args, R, dev, stream)
+
     # ---------------- the batched workload (many utterances, mixed M, uneven J)
     if not args.no_batch and args.rule == "accel" and ws == 1 and args.workload != "batch-256":
         result["batch"] = batch_section(args, R, dev, peaks, flush, stream)
@@ -708,6 +713,61 @@ def combine_ranks(res, slots, n_iter, dev):
     out.update(ms_per_step=float(mx[0]), value=float(t[1]) * n_iter / (float(mx[0]) / 1e3),
                h2d_bytes_per_step=int(t[2]), d2h_bytes_per_step=int(t[3]))
     out["api"] = res["api"] + ", every rank on its own frequency rows; slowest rank's step"
+    return out
+
+
+def front_section(args, R, dev, stream, seconds=8.7):
+    """The front end at the paper's settings (Sec. IV-A, Table II): M = 4, 16 kHz, a
+    mixture of 8.7 s, 64 ms Hamming window with a 32 ms shift (n_fft 1024), K = 10,
+    50 ILRMA iterations; then the estimator's inputs from ILRMA's outputs, 200 EM
+    passes of Algorithm 2 (the paper's cap for the methods after ILRMA) and the
+    Wiener filter, and the inverse STFT of the target.  Each stage and the whole
+    chain from the time signal to the target's time signal are timed with CUDA
+    events (best of a few runs)."""
+    import torch
+    from paper_1908_01964_gb300 import synth
+    M, n_fft, shift, K, n_ilrma, n_em = 4, 1024, 512, 10, 50, 200
+    d = synth.make_time_mixture(M, int(16000 * seconds), 7)
+    sig = torch.from_numpy(d["sig"].astype(np.float32)).to(dev)
+    fe = R.Front(M, sig.shape[1], n_fft, shift, K)
+    T0, V0 = synth.ilrma_init_values(fe.I, fe.J, M, K, 8)
+    T0 = torch.from_numpy(T0.astype(np.float32)).to(dev)
+    V0 = torch.from_numpy(V0.astype(np.float32)).to(dev)
+    X = fe.stft(sig)
+    h = torch.empty_like(X)
+    state = {}
+
+    def chain():
+        fe.stft(sig, out=X)
+        W, T, V = fe.ilrma(X, T0, V0, n_ilrma)
+        (init,) = R.ilrma_init([dict(x=X, W=W, T=T[0], V=V[0], n_h=0)])
+        prob = dict(x=X, a=init["a"], Rp=init["Rp"], rh0=init["rh0"], ru0=init["ru0"])
+        with R.Solver([prob]) as s:
+            s.solve(n_em, out=h.view(-1))
+            state["status"] = s.status()
+        return fe.istft(h)
+
+    def timed(fn, reps):
+        best = float("inf")
+        for k in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k > 0:
+                best = min(best, e0.elapsed_time(e1))
+        return best
+    out = {"config": f"M={M}, {seconds} s at 16 kHz, n_fft {n_fft}, shift {shift}, K={K}, {n_ilrma} ILRMA "
+                     f"iterations, {n_em} EM passes (I={fe.I}, J={fe.J})",
+           "stft_ms": timed(lambda: fe.stft(sig, out=X), 5),
+           "ilrma_ms": timed(lambda: fe.ilrma(X, T0, V0, n_ilrma), 3),
+           "istft_ms": timed(lambda: fe.istft(X), 5),
+           "chain_ms": timed(chain, 3)}
+    out["status"] = R.strerror(state.get("status", 0))
+    out["realtime_factor"] = seconds * 1e3 / out["chain_ms"]
+    fe.close()
     return out
 
 

@@ -70,7 +70,9 @@ int rcscm_front_istft(rcscm_front* f, const void* X, float* out, void* stream);
  * target output is identified).  Per-slot sums and the NMF updates in FP32, the
  * covariance, the eigendecomposition and each M x M solve in FP64.  `status` (a
  * device int or NULL) receives RCSCM_ENONFINITE's bit if a non-finite or
- * non-positive value appears.  T, V may alias T0, V0. */
+ * non-positive value appears.  T, V may alias T0, V0.  The context captures the
+ * call's launches into a CUDA graph and replays it while the arguments' addresses
+ * and n_iter stay the same (new contents at the same addresses are read anew). */
 int rcscm_front_ilrma(rcscm_front* f, const void* X, const float* T0, const float* V0, int n_iter, void* W,
                       float* T, float* V, int* status, void* stream);
 

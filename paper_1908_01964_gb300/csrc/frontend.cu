@@ -395,40 +395,49 @@ __global__ void __launch_bounds__(256) t_update_kernel(const float* __restrict__
     }
 }
 
-// Activations of source n, one CTA of 8 warps per tile of 32 frames (lane = frame),
-// the warps splitting the frequencies; T_n [I][K] staged in shared memory (dynamic):
-//   v_kj <- max(v_kj sqrt( sum_i p_ij t_ik / r_ij^2 / sum_i t_ik / r_ij ), floor).
-__global__ void __launch_bounds__(256) v_update_kernel(const float* __restrict__ T, const float* __restrict__ P,
-                                                       float* __restrict__ V, int I, int J, int K) {
-    extern __shared__ float smem[];
-    float* sT = smem;                                   // [I][K]
-    float* red = smem + (size_t)I * K;                  // [8][2K][32]
-    for (int e = threadIdx.x; e < I * K; e += blockDim.x) sT[e] = T[e];
+// Activations of source n in two kernels.  v_partial_kernel: a CTA of 8 warps per tile of
+// 32 frames (lane = frame) and range of frequencies (blockIdx.y of nsplit), the warps
+// splitting the range; it writes the range's sums
+//   part[s][k][j] = sum_i p_ij t_ik / r_ij^2,  part[s][K + k][j] = sum_i t_ik / r_ij.
+// v_finish_kernel adds the ranges in order and updates
+//   v_kj <- max(v_kj sqrt( sum_s part[s][k][j] / sum_s part[s][K + k][j] ), floor).
+__global__ void __launch_bounds__(256) v_partial_kernel(const float* __restrict__ T, const float* __restrict__ P,
+                                                        const float* __restrict__ V, int I, int J, int K, int nsplit,
+                                                        float* __restrict__ part) {
+    __shared__ float sT[64 * kFrontMaxK];
+    __shared__ float red[8 * 2 * kFrontMaxK * 32];
+    const int s = blockIdx.y;
+    const int i0 = (int)((int64_t)I * s / nsplit), i1 = (int)((int64_t)I * (s + 1) / nsplit);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int j = blockIdx.x * 32 + lane;
     const bool on = j < J;
     float vk[kFrontMaxK];
 #pragma unroll
     for (int k = 0; k < kFrontMaxK; ++k) vk[k] = (on && k < K) ? V[(int64_t)k * J + j] : 0.f;
-    __syncthreads();
     float num[kFrontMaxK], den[kFrontMaxK];
 #pragma unroll
     for (int k = 0; k < kFrontMaxK; ++k) num[k] = den[k] = 0.f;
-    if (on) {
-        for (int i = warp; i < I; i += 8) {
-            const float* t = sT + (size_t)i * K;
-            float r = 0.f;
+    for (int c0 = i0; c0 < i1; c0 += 64) {           // stage up to 64 frequencies of T at a time
+        const int c1 = min(i1, c0 + 64);
+        __syncthreads();
+        for (int e = threadIdx.x; e < (c1 - c0) * K; e += blockDim.x) sT[e] = T[(int64_t)c0 * K + e];
+        __syncthreads();
+        if (on) {
+            for (int i = c0 + warp; i < c1; i += 8) {
+                const float* t = sT + (size_t)(i - c0) * K;
+                float r = 0.f;
 #pragma unroll
-            for (int k = 0; k < kFrontMaxK; ++k)
-                if (k < K) r = fmaf(t[k], vk[k], r);
-            const float ir = 1.0f / r;
-            const float pr = P[(int64_t)i * J + j] * ir * ir;
+                for (int k = 0; k < kFrontMaxK; ++k)
+                    if (k < K) r = fmaf(t[k], vk[k], r);
+                const float ir = 1.0f / r;
+                const float pr = P[(int64_t)i * J + j] * ir * ir;
 #pragma unroll
-            for (int k = 0; k < kFrontMaxK; ++k)
-                if (k < K) {
-                    num[k] = fmaf(pr, t[k], num[k]);
-                    den[k] = fmaf(ir, t[k], den[k]);
-                }
+                for (int k = 0; k < kFrontMaxK; ++k)
+                    if (k < K) {
+                        num[k] = fmaf(pr, t[k], num[k]);
+                        den[k] = fmaf(ir, t[k], den[k]);
+                    }
+            }
         }
     }
 #pragma unroll
@@ -438,16 +447,24 @@ __global__ void __launch_bounds__(256) v_update_kernel(const float* __restrict__
             red[((size_t)warp * 2 * K + K + k) * 32 + lane] = den[k];
         }
     __syncthreads();
-    if (warp == 0 && on) {
-        for (int k = 0; k < K; ++k) {
-            float a = 0.f, b = 0.f;
-            for (int w = 0; w < 8; ++w) {
-                a += red[((size_t)w * 2 * K + k) * 32 + lane];
-                b += red[((size_t)w * 2 * K + K + k) * 32 + lane];
-            }
-            V[(int64_t)k * J + j] = fmaxf(vk[k] * sqrtf(a / b), kNmfFloor);
+    if (on)
+        for (int q = warp; q < 2 * K; q += 8) {
+            float a = 0.f;
+            for (int w = 0; w < 8; ++w) a += red[((size_t)w * 2 * K + q) * 32 + lane];
+            part[((int64_t)s * 2 * K + q) * J + j] = a;
         }
+}
+
+__global__ void v_finish_kernel(const float* __restrict__ part, int J, int K, int nsplit, float* __restrict__ V) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)K * J) return;
+    const int k = (int)(e / J), j = (int)(e % J);
+    float a = 0.f, b = 0.f;
+    for (int s = 0; s < nsplit; ++s) {
+        a += part[((int64_t)s * 2 * K + k) * J + j];
+        b += part[((int64_t)s * 2 * K + K + k) * J + j];
     }
+    V[e] = fmaxf(V[e] * sqrtf(a / b), kNmfFloor);
 }
 
 // Demixing row n, one CTA per frequency i (iterative projection):
@@ -463,6 +480,7 @@ __global__ void __launch_bounds__(256) w_update_kernel(const float2* __restrict_
     __shared__ float red[9 * 2 * NU];
     __shared__ float2 sw[M];
     __shared__ float redp[9];
+    __shared__ double2 sU[M][M], sB[M][M + 1], sF[M];
     const int i = blockIdx.x;
     if (threadIdx.x < K) sT[threadIdx.x] = T[(int64_t)i * K + threadIdx.x];
     __syncthreads();
@@ -488,65 +506,85 @@ __global__ void __launch_bounds__(256) w_update_kernel(const float2* __restrict_
             }
     }
     block_sum_fv<2 * NU>(acc, red);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {                           // FP64 solve by the lanes of warp 0
+        const int lane = threadIdx.x;
         const float* tot = red + 8 * 2 * NU;
-        double2 U[M][M], B[M][M + 1];
-        int q = 0;
-        for (int a = 0; a < M; ++a)
-            for (int b = a; b < M; ++b) {
-                const double2 v = make_double2((double)tot[2 * q] / J, (double)tot[2 * q + 1] / J);
-                U[a][b] = v;
-                U[b][a] = zconj(v);
-                ++q;
+        if (lane < NU) {                              // U (Hermitian) from its upper triangle
+            int a = 0, q = lane;
+            while (q >= M - a) {
+                q -= M - a;
+                ++a;
             }
+            const int b = a + q;
+            const double2 v = make_double2((double)tot[2 * lane] / J, (double)tot[2 * lane + 1] / J);
+            sU[a][b] = v;
+            sU[b][a] = zconj(v);
+        }
+        __syncwarp();
         const double2* Wi = W + (int64_t)i * M * M;
-        for (int a = 0; a < M; ++a) {                  // [W_i U | e_n]
-            for (int b = 0; b < M; ++b) {
-                double2 s = make_double2(0.0, 0.0);
-                for (int k = 0; k < M; ++k) s = zfma(s, Wi[a * M + k], U[k][b]);
-                B[a][b] = s;
-            }
-            B[a][M] = make_double2(a == n ? 1.0 : 0.0, 0.0);
+        for (int e = lane; e < M * (M + 1); e += 32) {   // [W_i U | e_n]
+            const int a = e / (M + 1), b = e % (M + 1);
+            double2 v = make_double2(b == M && a == n ? 1.0 : 0.0, 0.0);
+            if (b < M)
+                for (int k = 0; k < M; ++k) v = zfma(v, Wi[a * M + k], sU[k][b]);
+            sB[a][b] = v;
         }
+        __syncwarp();
         bool bad = false;
-        for (int c = 0; c < M; ++c) {                  // Gauss-Jordan with partial pivoting
-            int piv = c;
-            for (int r2 = c + 1; r2 < M; ++r2)
-                if (zabs2(B[r2][c]) > zabs2(B[piv][c])) piv = r2;
-            if (piv != c)
-                for (int b = 0; b <= M; ++b) {
-                    const double2 t = B[c][b];
-                    B[c][b] = B[piv][b];
-                    B[piv][b] = t;
+        for (int c = 0; c < M; ++c) {                 // Gauss-Jordan with partial pivoting
+            // pivot: the largest |B_rc| over r >= c (magnitudes compared in FP32 across lanes)
+            float mag = lane >= c && lane < M ? (float)zabs2(sB[lane][c]) : -1.f;
+            int idx = lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float om = __shfl_xor_sync(0xffffffffu, mag, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+                if (om > mag || (om == mag && oi < idx)) {
+                    mag = om;
+                    idx = oi;
                 }
-            const double d2 = zabs2(B[c][c]);
-            bad |= !(d2 > 0.0);
-            const double2 inv = d2 > 0.0 ? make_double2(B[c][c].x / d2, -B[c][c].y / d2) : make_double2(0.0, 0.0);
-            for (int b = c; b <= M; ++b) B[c][b] = zmul(B[c][b], inv);
-            for (int r2 = 0; r2 < M; ++r2) {
-                if (r2 == c) continue;
-                const double2 f = B[r2][c];
-                for (int b = c; b <= M; ++b) B[r2][b] = zsub(B[r2][b], zmul(f, B[c][b]));
             }
+            const int piv = idx;
+            if (piv != c)
+                for (int b = lane; b <= M; b += 32) {
+                    const double2 t = sB[c][b];
+                    sB[c][b] = sB[piv][b];
+                    sB[piv][b] = t;
+                }
+            __syncwarp();
+            const double2 pv = sB[c][c];
+            const double d2 = zabs2(pv);
+            bad |= !(d2 > 0.0);
+            const double2 inv = d2 > 0.0 ? make_double2(pv.x / d2, -pv.y / d2) : make_double2(0.0, 0.0);
+            if (lane < M) sF[lane] = sB[lane][c];     // the column's factors, before it is cleared
+            __syncwarp();
+            for (int b = lane; b <= M; b += 32) sB[c][b] = zmul(sB[c][b], inv);
+            __syncwarp();
+            for (int e = lane; e < M * (M + 1); e += 32) {
+                const int r = e / (M + 1), b = e % (M + 1);
+                if (r != c && b >= c) sB[r][b] = zsub(sB[r][b], zmul(sF[r], sB[c][b]));
+            }
+            __syncwarp();
         }
-        double2 w[M];
-        for (int a = 0; a < M; ++a) w[a] = B[a][M];
-        double quad = 0.0;                             // w^H U w
-        for (int a = 0; a < M; ++a) {
-            double2 s = make_double2(0.0, 0.0);
-            for (int b = 0; b < M; ++b) s = zfma(s, U[a][b], w[b]);
-            quad += w[a].x * s.x + w[a].y * s.y;
+        double qp = 0.0;                              // w^H U w
+        if (lane < M) {
+            double2 uw = make_double2(0.0, 0.0);
+            for (int b = 0; b < M; ++b) uw = zfma(uw, sU[lane][b], sB[b][M]);
+            qp = sB[lane][M].x * uw.x + sB[lane][M].y * uw.y;
         }
-        bad |= !(quad > 0.0) || !(quad <= DBL_MAX);
-        const double sc = quad > 0.0 ? 1.0 / sqrt(quad) : 0.0;
-        for (int a = 0; a < M; ++a) {                  // row n = w^H
-            const double2 v = make_double2(w[a].x * sc, -w[a].y * sc);
-            W[(int64_t)i * M * M + n * M + a] = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qp += __shfl_xor_sync(0xffffffffu, qp, o);
+        bad |= !(qp > 0.0) || !(qp <= DBL_MAX);
+        const double sc = qp > 0.0 ? 1.0 / sqrt(qp) : 0.0;
+        if (lane < M) {                               // row n = w^H
+            const double2 w = sB[lane][M];
+            const double2 v = make_double2(w.x * sc, -w.y * sc);
+            W[(int64_t)i * M * M + n * M + lane] = v;
             const float2 vf = make_float2((float)v.x, (float)v.y);
-            W32[(int64_t)i * M * M + n * M + a] = vf;
-            sw[a] = vf;
+            W32[(int64_t)i * M * M + n * M + lane] = vf;
+            sw[lane] = vf;
         }
-        if (bad) atomicOr(status, kFlagNonfinite);
+        if (lane == 0 && bad) atomicOr(status, kFlagNonfinite);
     }
     __syncthreads();
     float ps = 0.f;
@@ -564,26 +602,39 @@ __global__ void __launch_bounds__(256) w_update_kernel(const float2* __restrict_
     if (threadIdx.x == 0) sumP[i] = (double)redp[8];
 }
 
-// Scale normalisation after the iteration, one CTA per frequency:
-//   lambda_n^2 = (1/(IJ)) sum_ij p_ijn;  w_in /= lambda_n, t_ikn /= lambda_n^2, p_ijn /= lambda_n^2.
-template <int M>
-__global__ void __launch_bounds__(256) normalise_kernel(const double* __restrict__ sumP, int I, int J, int K,
-                                                        double2* __restrict__ W, float2* __restrict__ W32,
-                                                        float* __restrict__ T, float* __restrict__ P, int* status) {
-    __shared__ double slam[M];
-    const int i = blockIdx.x;
-    if (threadIdx.x < M) {
-        const int n = threadIdx.x;
-        double s = 0.0;
-        for (int k = 0; k < I; ++k) s += sumP[(int64_t)n * I + k];
-        const double l2 = s / ((double)I * (double)J);
-        slam[n] = l2;
-        if (!(l2 > 0.0) || !(l2 <= DBL_MAX)) atomicOr(status, kFlagNonfinite);
+// Scale factors of the normalisation: lam2[n] = (1/(IJ)) sum_ij p_ijn, from the row sums
+// of the demixing update, one CTA, FP64 tree in a fixed order.
+__global__ void __launch_bounds__(256) scale_kernel(const double* __restrict__ sumP, int N, int I, int J,
+                                                    double* __restrict__ lam2, int* status) {
+    __shared__ double red[256];
+    for (int n = 0; n < N; ++n) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < I; i += blockDim.x) v += sumP[(int64_t)n * I + i];
+        red[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const double l2 = red[0] / ((double)I * (double)J);
+            lam2[n] = l2;
+            if (!(l2 > 0.0) || !(l2 <= DBL_MAX)) atomicOr(status, kFlagNonfinite);
+        }
+        __syncthreads();
     }
-    __syncthreads();
+}
+
+// Scale normalisation after the iteration, one CTA per frequency:
+//   w_in /= lambda_n, t_ikn /= lambda_n^2, p_ijn /= lambda_n^2.
+template <int M>
+__global__ void __launch_bounds__(256) normalise_kernel(const double* __restrict__ lam2, int I, int J, int K,
+                                                        double2* __restrict__ W, float2* __restrict__ W32,
+                                                        float* __restrict__ T, float* __restrict__ P) {
+    const int i = blockIdx.x;
     if (threadIdx.x < M * M) {
         const int n = threadIdx.x / M;
-        const double il = slam[n] > 0.0 ? 1.0 / sqrt(slam[n]) : 1.0;
+        const double il = lam2[n] > 0.0 ? 1.0 / sqrt(lam2[n]) : 1.0;
         const int64_t o = (int64_t)i * M * M + threadIdx.x;
         const double2 v = zscale(W[o], il);
         W[o] = v;
@@ -591,7 +642,7 @@ __global__ void __launch_bounds__(256) normalise_kernel(const double* __restrict
     }
     const int64_t S = (int64_t)I * J;
     for (int n = 0; n < M; ++n) {
-        const float il2 = slam[n] > 0.0 ? (float)(1.0 / slam[n]) : 1.f;
+        const float il2 = lam2[n] > 0.0 ? (float)(1.0 / lam2[n]) : 1.f;
         if (threadIdx.x < K) T[((int64_t)n * I + i) * K + threadIdx.x] *= il2;
         for (int j = threadIdx.x; j < J; j += blockDim.x) P[(int64_t)n * S + (int64_t)i * J + j] *= il2;
     }
@@ -629,7 +680,16 @@ struct rcscm_front {
     float* P = nullptr;          // [N][I][J] |y|^2
     double* sumP = nullptr;      // [N][I] row sums of P
     int* status = nullptr;       // [1] status word when the caller passes none
-    size_t v_smem = 0;           // dynamic shared memory of the activation update
+    double* lam2 = nullptr;      // [N] scale factors of the normalisation
+    float* vpart = nullptr;      // [nsplit][2K][J] partial sums of the activation update
+    int nsplit = 1;              // frequency ranges of the activation update
+    // rcscm_front_ilrma's launches captured as a CUDA graph, replayed while its arguments
+    // (addresses and iteration count) stay the same
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void* gkey[8] = {};
+    int giter = -1;
 };
 
 namespace {
@@ -648,6 +708,11 @@ void front_free(rcscm_front* f) {
     cudaFree(f->P);
     cudaFree(f->sumP);
     cudaFree(f->status);
+    cudaFree(f->lam2);
+    cudaFree(f->vpart);
+    if (f->gexec) cudaGraphExecDestroy(f->gexec);
+    if (f->graph) cudaGraphDestroy(f->graph);
+    if (f->cap) cudaStreamDestroy(f->cap);
     delete f;
 }
 
@@ -668,10 +733,12 @@ cudaError_t ilrma_launches(rcscm_front* f, const float2* X, float* T, float* V, 
             float* Vn = V + (int64_t)n * K * J;
             float* Pn = f->P + (int64_t)n * S;
             t_update_kernel<<<I, 256, 0, s>>>(Vn, Pn, Tn, J, K);
-            v_update_kernel<<<vt, 256, f->v_smem, s>>>(Tn, Pn, Vn, I, J, K);
+            v_partial_kernel<<<dim3(vt, f->nsplit), 256, 0, s>>>(Tn, Pn, Vn, I, J, K, f->nsplit, f->vpart);
+            v_finish_kernel<<<(K * J + 255) / 256, 256, 0, s>>>(f->vpart, J, K, f->nsplit, Vn);
             w_update_kernel<M><<<I, 256, 0, s>>>(f->Xs, Tn, Vn, n, J, K, f->W, f->W32, Pn, f->sumP + (int64_t)n * I, st);
         }
-        normalise_kernel<M><<<I, 256, 0, s>>>(f->sumP, I, J, K, f->W, f->W32, T, f->P, st);
+        scale_kernel<<<1, 256, 0, s>>>(f->sumP, M, I, J, f->lam2, st);
+        normalise_kernel<M><<<I, 256, 0, s>>>(f->lam2, I, J, K, f->W, f->W32, T, f->P);
         e = cudaGetLastError();
     }
     const int64_t nw = (int64_t)I * M * M;
@@ -687,6 +754,9 @@ int map_err(cudaError_t e) {
     }
     return RCSCM_ECUDA;
 }
+
+int ilrma_enqueue(rcscm_front* f, const void* vx, const void* vt0, const void* vv0, int n_iter, const void* vw,
+                  const void* vt, const void* vv, const void* vst, cudaStream_t s);
 
 }  // namespace
 
@@ -723,9 +793,12 @@ int rcscm_front_create(rcscm_front** out, int64_t M, int64_t n_samples, int n_ff
     if (e == cudaSuccess) e = cudaMalloc(&f->P, Mz * S * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&f->sumP, Mz * I * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&f->status, sizeof(int));
-    f->v_smem = (I * (size_t)K + 8 * 2 * (size_t)K * 32) * sizeof(float);
-    if (e == cudaSuccess && f->v_smem > 48 * 1024)
-        e = cudaFuncSetAttribute(v_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->v_smem);
+    if (e == cudaSuccess) e = cudaMalloc(&f->lam2, Mz * sizeof(double));
+    // the activation update's frequency ranges: about two CTAs per SM of 152, at least 8
+    // frequencies per range
+    const int tiles = (int)((J + 31) / 32);
+    f->nsplit = std::max(1, std::min((int)(I / 8), (304 + tiles - 1) / tiles));
+    if (e == cudaSuccess) e = cudaMalloc(&f->vpart, (size_t)f->nsplit * 2 * K * J * sizeof(float));
     const size_t fft_smem = (size_t)n_fft * sizeof(float2);
     if (e == cudaSuccess && fft_smem > 48 * 1024) {
         e = cudaFuncSetAttribute(stft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem);
@@ -782,6 +855,44 @@ int rcscm_front_ilrma(rcscm_front* f, const void* X, const float* T0, const floa
         front_view(W, &vw) || front_view(T, &vt) || front_view(V, &vv) || (status && front_view(status, &vst)))
         return RCSCM_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const void* key[8] = {vx, vt0, vv0, vw, vt, vv, vst, nullptr};
+    bool same = f->gexec && f->giter == n_iter;
+    for (int k = 0; k < 8 && same; ++k) same = f->gkey[k] == key[k];
+    if (same) return map_err(cudaGraphLaunch(f->gexec, s));
+    // capture the launches on the context's own stream, then replay the graph on `stream`
+    cudaError_t e = cudaSuccess;
+    if (!f->cap) e = cudaStreamCreateWithFlags(&f->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(f->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return map_err(e);
+    const int st = ilrma_enqueue(f, vx, vt0, vv0, n_iter, vw, vt, vv, vst, f->cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(f->cap, &g);
+    if (st != RCSCM_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return st != RCSCM_OK ? st : map_err(e);
+    }
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return map_err(e);
+    }
+    if (f->gexec) cudaGraphExecDestroy(f->gexec);
+    if (f->graph) cudaGraphDestroy(f->graph);
+    f->graph = g;
+    f->gexec = x;
+    f->giter = n_iter;
+    for (int k = 0; k < 8; ++k) f->gkey[k] = key[k];
+    return map_err(cudaGraphLaunch(f->gexec, s));
+}
+
+}  // extern "C"
+
+namespace {
+
+// The work of rcscm_front_ilrma on stream s (captured into the context's graph).
+int ilrma_enqueue(rcscm_front* f, const void* vx, const void* vt0, const void* vv0, int n_iter, const void* vw,
+                  const void* vt, const void* vv, const void* vst, cudaStream_t s) {
     const size_t nT = (size_t)f->M * f->I * f->K * sizeof(float), nV = (size_t)f->M * f->K * f->J * sizeof(float);
     cudaError_t e = cudaSuccess;
     if (vt != vt0) e = cudaMemcpyAsync(const_cast<void*>(vt), vt0, nT, cudaMemcpyDefault, s);
@@ -805,4 +916,4 @@ int rcscm_front_ilrma(rcscm_front* f, const void* X, const float* T0, const floa
     return map_err(e);
 }
 
-}  // extern "C"
+}  // namespace
