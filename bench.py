@@ -367,9 +367,12 @@ def cpu_baseline(p, wl, rule):
 
 # ----------------------------------------------------------------------------- our arm
 
-def time_steps(solver, h, n_iter, K, W, flush, stream, sampler=None, preroll_s=0.0, graph=False, fused=False):
+def time_steps(solver, h, n_iter, K, W, flush, stream, sampler=None, preroll_s=0.0, graph=False, fused=False,
+               whole=False):
     """Returns (one, names): one(record) runs a step and, if record, returns its
-    CUDA events (start, then one per segment in `names`)."""
+    CUDA events (start, then one per segment in `names`).  whole: only the start and
+    the end of the step are recorded (an event between the setup and the fused kernel
+    would hold the fused kernel back until the setup ends)."""
     import torch
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     if graph:
@@ -390,7 +393,7 @@ def time_steps(solver, h, n_iter, K, W, flush, stream, sampler=None, preroll_s=0
             e[0].record(stream)
         for k, call in enumerate(calls):
             call()
-            if record:
+            if record and (not whole or k == len(calls) - 1):
                 e[k + 1].record(stream)
         return e
 
@@ -495,7 +498,7 @@ def run_ours(args):
         sampler.wait_first()
     fused = (args.path == "fused" and args.rule == "accel" and args.iters_per_launch == 0)
     one, seg_names = time_steps(solver, h, n_iter, args.steps, args.warmup, flush, stream, sampler,
-                                args.clock_preroll, graph=args.graph, fused=fused)
+                                args.clock_preroll, graph=args.graph, fused=fused, whole=fused)
     barrier()
     torch.cuda.synchronize()
     if sampler:
@@ -510,7 +513,14 @@ def run_ours(args):
     if code not in (R.OK, R.ECLAMP):
         raise RuntimeError(f"device status after the timed steps: {R.strerror(code)}")
     step_ms = [e[0].elapsed_time(e[-1]) for e in events]
-    seg = {k: [e[i].elapsed_time(e[i + 1]) for e in events] for i, k in enumerate(seg_names)}
+    if fused:        # each kernel alone: a few more steps with an event between the two launches
+        one_seg, _ = time_steps(solver, h, n_iter, 0, 0, flush, stream, fused=True)
+        torch.cuda.synchronize()
+        seg_events = [one_seg(True) for _ in range(max(5, min(args.steps, 20)))]
+        torch.cuda.synchronize()
+        seg = {k: [e[i].elapsed_time(e[i + 1]) for e in seg_events] for i, k in enumerate(seg_names)}
+    else:
+        seg = {k: [e[i].elapsed_time(e[i + 1]) for e in events] for i, k in enumerate(seg_names)}
     total_ms = sum(step_ms)
     if ws > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)

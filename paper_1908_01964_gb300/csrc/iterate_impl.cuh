@@ -115,12 +115,30 @@ __global__ void __launch_bounds__(BLOCK) accel_kernel(DevState d, int n_iter, It
     accel_one_row<BLOCK, SPT, false>(d, d.order[blockIdx.x], n_iter, p, red, nullptr, nullptr);
 }
 
+// Launched as a programmatic dependent of the per-frequency setup: a CTA may start while
+// the setup still runs.  Before griddepcontrol.wait it touches only the caller's inputs,
+// and only to ask L2 for them (prefetch: no value is read, so a preceding kernel that
+// writes them is still seen); every setup output is read after the wait.
 template <int BLOCK, int SPT>
 __global__ void __launch_bounds__(BLOCK, solve_min_blocks(BLOCK, SPT)) solve_kernel(DevState d, int n_iter, IterParams p, float2* h) {
     __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
     __shared__ FusedSmem fs;
-    RCSCM_CTA_CHECK(row_ok(d, d.order[blockIdx.x], BLOCK * SPT), d.status);
-    accel_one_row<BLOCK, SPT, true>(d, d.order[blockIdx.x], n_iter, p, red, h, &fs);
+    const int r = d.order[blockIdx.x];
+    RCSCM_CTA_CHECK(row_ok(d, r, BLOCK * SPT), d.status);
+    {
+        const RowDesc* rd = d.rows + r;
+        const char* xb = reinterpret_cast<const char*>(rd->x);
+        const int64_t xbytes = (int64_t)rd->J * rd->M * (int64_t)sizeof(float2);
+        for (int64_t o = (int64_t)threadIdx.x * 128; o < xbytes; o += (int64_t)BLOCK * 128)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(xb + o));
+        const int64_t sbytes = (int64_t)rd->J * (int64_t)sizeof(float);
+        for (int64_t o = (int64_t)threadIdx.x * 128; o < sbytes; o += (int64_t)BLOCK * 128) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(rd->rh0) + o));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(rd->ru0) + o));
+        }
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    accel_one_row<BLOCK, SPT, true>(d, r, n_iter, p, red, h, &fs);
 }
 
 #include "stream_kernel.cuh"
@@ -172,9 +190,19 @@ template <int BLOCK, int SPT>
 cudaError_t launch_accel_t(const DevState& d, int n_rows, int n_iter, const IterParams& p, bool persistent,
                            float2* h, cudaStream_t s) {
     if (!persistent) {
-        if (h)
-            solve_kernel<BLOCK, SPT><<<n_rows, BLOCK, 0, s>>>(d, n_iter, p, h);
-        else if (n_iter == 1)
+        if (h) {                  // a programmatic dependent of the kernel before it (the setup)
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(n_rows);
+            cfg.blockDim = dim3(BLOCK);
+            cfg.dynamicSmemBytes = 0;
+            cfg.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            return cudaLaunchKernelEx(&cfg, solve_kernel<BLOCK, SPT>, d, n_iter, p, h);
+        } else if (n_iter == 1)
             accel_stream_kernel<BLOCK, SPT><<<n_rows, BLOCK, 0, s>>>(d, p);
         else
             accel_kernel<BLOCK, SPT><<<n_rows, BLOCK, 0, s>>>(d, n_iter, p);

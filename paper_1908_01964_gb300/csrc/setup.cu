@@ -249,6 +249,8 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     __shared__ float2 sb32[kSetupRows][kMaxM];
     __shared__ int sperm[kSetupRows][kMaxM];
 
+    // the fused row kernel that follows may start now: it waits for this grid's results
+    asm volatile("griddepcontrol.launch_dependents;");
     const int g = threadIdx.x / kGroupLanes;
     const int l = threadIdx.x % kGroupLanes;
     const int r = blockIdx.x * kSetupRows + g;
