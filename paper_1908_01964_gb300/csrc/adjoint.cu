@@ -94,7 +94,7 @@ struct AdjShared {
 
 template <int BLOCK, int NP, int SPT>
 __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs& g, const IterParams& p, int r,
-                                            AdjShared<BLOCK, SPT>& sh) {
+                                            AdjShared<BLOCK, SPT>& sh, float* segsm) {
     constexpr int NK = 2 * NP;
     float (*red)[BLOCK / 32] = sh.red;
     float (*redn)[BLOCK / 32][8] = sh.redn;
@@ -243,9 +243,21 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
 
     // ---- 2. passes t = K-1 .. 0, one checkpoint segment at a time ----------------------------
     // Each segment is recomputed once from its checkpoint with the forward pass code; the
-    // state entering each of its passes goes to the segment scratch (each thread its own
+    // state entering each of its passes goes to the segment buffer (each thread its own
     // slots, lambda by thread 0, read after the passes' barriers), then the passes are
-    // reversed from the scratch.
+    // reversed from the buffer.  The buffer is the CTA's shared memory when the launch gave
+    // it room (segsm != nullptr: [stride][SPT * BLOCK] r_h, then r_u, then [stride] lambda),
+    // else the context's scratch in global memory.
+    constexpr int kPitch = SPT * BLOCK;
+    auto seg_rh_at = [&](int tt) -> float* {
+        return segsm ? segsm + (size_t)tt * kPitch : g.seg_rh + (size_t)tt * g.S + off;
+    };
+    auto seg_ru_at = [&](int tt) -> float* {
+        return segsm ? segsm + (size_t)(g.stride + tt) * kPitch : g.seg_ru + (size_t)tt * g.S + off;
+    };
+    auto seg_lam_at = [&](int tt) -> float* {
+        return segsm ? segsm + (size_t)2 * g.stride * kPitch + tt : g.seg_lam + (size_t)tt * g.R + r;
+    };
     int parity = 1;                                                 // the next reduction uses half 1
     const int n_seg = (g.K + g.stride - 1) / g.stride;
     for (int seg = n_seg - 1; seg >= 0; --seg) {
@@ -253,8 +265,8 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
         st.load_state(g.ckpt_rh + (size_t)seg * g.S + off, g.ckpt_ru + (size_t)seg * g.S + off,
                       g.ckpt_lam[(size_t)seg * g.R + r]);
         for (int t = t0; t < t1; ++t) {
-            st.store_state(g.seg_rh + (size_t)(t - t0) * g.S + off, g.seg_ru + (size_t)(t - t0) * g.S + off);
-            if (tid == 0) g.seg_lam[(size_t)(t - t0) * g.R + r] = st.lam;
+            st.store_state(seg_rh_at(t - t0), seg_ru_at(t - t0));
+            if (tid == 0) *seg_lam_at(t - t0) = st.lam;
             st.pass(c, p, red, (parity++) & 1);
         }
         const float lam_end = st.lam;                               // lambda after pass t1 - 1
@@ -262,16 +274,16 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
             // state entering pass t, and lambda after it
             float rh_t[NK], ru_t[NK];
             {
-                const float* srh = g.seg_rh + (size_t)(t - t0) * g.S + off;
-                const float* sru = g.seg_ru + (size_t)(t - t0) * g.S + off;
+                const float* srh = seg_rh_at(t - t0);
+                const float* sru = seg_ru_at(t - t0);
 #pragma unroll
                 for (int k = 0; k < NK; ++k) {
                     rh_t[k] = valid[k] ? srh[k * BLOCK + tid] : 0.f;
                     ru_t[k] = valid[k] ? sru[k * BLOCK + tid] : 1.f;
                 }
             }
-            const float lam_t = g.seg_lam[(size_t)(t - t0) * g.R + r];
-            const float lam1 = t == t1 - 1 ? lam_end : g.seg_lam[(size_t)(t + 1 - t0) * g.R + r];
+            const float lam_t = *seg_lam_at(t - t0);
+            const float lam1 = t == t1 - 1 ? lam_end : *seg_lam_at(t + 1 - t0);
             const float il = rcp_refined(lam_t);
             const float rtaa = fmaf(c.sab2, il, c.taa);
             const float slr = c.sab_re * il, sli = c.sab_im * il;
@@ -547,25 +559,53 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
 
 // One CTA per row; the row's exact count of chunk pairs selects the body (as in the
 // forward kernel, so the recomputed states equal the forward ones bit for bit).
+// 128-thread rows are held to 4 CTAs per SM (128 registers; the row phases are latency
+// chains, so residency pays more than the few spilled values cost).
 template <int BLOCK, int SPT>
-__global__ void __launch_bounds__(BLOCK) adjoint_kernel(DevState d, AdjointArgs g, IterParams p) {
+__global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 4 : 1) adjoint_kernel(DevState d, AdjointArgs g, IterParams p, int seg_in_smem) {
     __shared__ AdjShared<BLOCK, SPT> sh;
+    extern __shared__ float segsm[];
+    float* seg = seg_in_smem ? segsm : nullptr;
     const int r = blockIdx.x;
     RCSCM_CTA_CHECK(row_ok(d, r, BLOCK * SPT), d.status);
     const int np = (d.rows[r].J + 2 * BLOCK - 1) / (2 * BLOCK);
     switch (np) {
-        case 1: adjoint_row<BLOCK, 1, SPT>(d, g, p, r, sh); break;
-        case 2: if constexpr (SPT >= 4) adjoint_row<BLOCK, 2, SPT>(d, g, p, r, sh); break;
-        case 3: if constexpr (SPT >= 8) adjoint_row<BLOCK, 3, SPT>(d, g, p, r, sh); break;
-        case 4: if constexpr (SPT >= 8) adjoint_row<BLOCK, 4, SPT>(d, g, p, r, sh); break;
+        case 1: adjoint_row<BLOCK, 1, SPT>(d, g, p, r, sh, seg); break;
+        case 2: if constexpr (SPT >= 4) adjoint_row<BLOCK, 2, SPT>(d, g, p, r, sh, seg); break;
+        case 3: if constexpr (SPT >= 8) adjoint_row<BLOCK, 3, SPT>(d, g, p, r, sh, seg); break;
+        case 4: if constexpr (SPT >= 8) adjoint_row<BLOCK, 4, SPT>(d, g, p, r, sh, seg); break;
         default: break;
     }
 }
 
+// The segment buffer goes to shared memory when it fits beside the kernel's static shared
+// memory within the per-block limit (and leaves room for the CTAs the registers allow).
 template <int BLOCK, int SPT>
 cudaError_t launch_adjoint_t(const DevState& d, int n_rows, const AdjointArgs& a, const IterParams& p,
                              cudaStream_t s) {
-    adjoint_kernel<BLOCK, SPT><<<n_rows, BLOCK, 0, s>>>(d, a, p);
+    const size_t bytes = ((size_t)2 * a.stride * SPT * BLOCK + (size_t)a.stride) * sizeof(float);
+    static size_t limit = 0;
+    static size_t static_bytes = 0;
+    if (!limit) {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+            cudaFuncGetAttributes(&fa, adjoint_kernel<BLOCK, SPT>) == cudaSuccess) {
+            static_bytes = fa.sharedSizeBytes;
+            limit = (size_t)optin > static_bytes ? (size_t)optin - static_bytes : 1;
+            if (cudaFuncSetAttribute(adjoint_kernel<BLOCK, SPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(limit > 1 ? limit : 0)) != cudaSuccess) {
+                cudaGetLastError();
+                limit = 1;
+            }
+        } else {
+            cudaGetLastError();
+            limit = 1;
+        }
+    }
+    const bool in_smem = bytes <= 96 * 1024 && bytes <= limit;
+    adjoint_kernel<BLOCK, SPT><<<n_rows, BLOCK, in_smem ? bytes : 0, s>>>(d, a, p, in_smem ? 1 : 0);
     return cudaGetLastError();
 }
 
