@@ -176,6 +176,8 @@ KERNEL_SOURCES = {
     "ilrma_init_kernel": ["ilrma.cu", "ilrma.cuh", "rcscm_internal.cuh"],
     "accel1_kernel": ["accel1.cu", "accel_common.cuh", "dfloat.cuh", "rcscm_internal.cuh"],
     "naive_white_kernel": ["naive.cu", "rcscm_internal.cuh"],
+    "w_update_kernel": ["frontend.cu", "rcscm_internal.cuh"],
+    "v_partial_kernel": ["frontend.cu", "rcscm_internal.cuh"],
     "invariants_kernel": ["setup.cu", "rcscm_internal.cuh"],
     "extract_kernel": ["extract.cu", "rcscm_internal.cuh"],
 }
