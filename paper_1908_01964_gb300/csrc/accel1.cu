@@ -97,7 +97,7 @@ __device__ __forceinline__ void apply_inverse(const float2 (*sC)[M], const float
 template <int BLOCK, int SPT, int M>
 __global__ void __launch_bounds__(BLOCK) accel1_kernel(DevState d, const int* __restrict__ rows, int n_iter,
                                                        IterParams p) {
-    __shared__ float red[2][BLOCK / 32];
+    __shared__ __align__(16) float red[2][BLOCK / 32];
     __shared__ dfc sRp[M][M], sL[M + 1][M + 1];
     __shared__ dfc sb[M], sa[M];
     __shared__ df sinv[M];

@@ -12,15 +12,29 @@
 
 namespace rcscm {
 
-// Sum over the block with one __syncthreads; `red` is double-buffered by the
-// pass parity so consecutive passes never race on it.  Every thread returns
-// the same, order-fixed value.  A single-warp block needs no shared memory.
+// Sum over the block with one __syncthreads; `red` (16-byte aligned) is double-buffered
+// by the pass parity so consecutive passes never race on it.  Every thread returns the
+// same, order-fixed value: the warp sums w_k combined as a butterfly over k, which for 4
+// and 8 warps is read back as one or two 16-byte words and added in the butterfly's order
+// (the same value, with a shorter dependency chain than two or three more shuffles).  A
+// single-warp block needs no shared memory.
 template <int BLOCK>
 __device__ __forceinline__ float block_sum(float v, float (*red)[BLOCK / 32 > 0 ? BLOCK / 32 : 1], int parity) {
     constexpr int NW = BLOCK / 32;
     v = warp_sum(v);
     if constexpr (NW == 1) {
         return v;
+    } else if constexpr (NW == 4) {
+        if ((threadIdx.x & 31) == 0) red[parity][threadIdx.x >> 5] = v;
+        __syncthreads();
+        const float4 w = *reinterpret_cast<const float4*>(&red[parity][0]);
+        return (w.x + w.z) + (w.y + w.w);
+    } else if constexpr (NW == 8) {
+        if ((threadIdx.x & 31) == 0) red[parity][threadIdx.x >> 5] = v;
+        __syncthreads();
+        const float4 a = *reinterpret_cast<const float4*>(&red[parity][0]);
+        const float4 b = *reinterpret_cast<const float4*>(&red[parity][4]);
+        return ((a.x + b.x) + (a.z + b.z)) + ((a.y + b.y) + (a.w + b.w));
     } else {
         const int lane = threadIdx.x & 31;
         if (lane == 0) red[parity][threadIdx.x >> 5] = v;
@@ -76,7 +90,8 @@ __device__ __forceinline__ f32x2 dup(float v) { return pk(v, v); }
 struct PassConsts {
     f32x2 NSR, NSI, SI, SAB2, NITAA, TAAM, CA2, CB, RTAA, SLR, SLI, NSLI;
 };
-__device__ __forceinline__ PassConsts pass_consts(const RowConst& c, const IterParams& p, float lam) {
+// il = rcp_refined(lambda) of the pass.
+__device__ __forceinline__ PassConsts pass_consts(const RowConst& c, const IterParams& p, float il) {
     PassConsts k;
     k.NSR = dup(-c.sab_re);
     k.NSI = dup(-c.sab_im);
@@ -86,7 +101,6 @@ __device__ __forceinline__ PassConsts pass_consts(const RowConst& c, const IterP
     k.TAAM = dup(c.taaM);
     k.CA2 = dup(p.c_a2);
     k.CB = dup(p.c_b);
-    const float il = rcp_refined(lam);
     k.RTAA = dup(fmaf(c.sab2, il, c.taa));                       // rho~_aa, Eq. (eq:traa_accel)
     const float slr = c.sab_re * il, sli = c.sab_im * il;
     k.SLR = dup(slr);
@@ -130,6 +144,7 @@ struct RowState {
     f32x2 tr[NP], ti[NP], sr[NP], si[NP], kapM[NP], rh[NP], ru[NP], B[NP];
     f32x2 CB_LAST;
     float lam;
+    float il;    // rcp_refined(lam), formed once per pass and used by this pass and the next
     int J;
 
     // Invariants tau_ax, sigma_bx and kappa/M (+ r_u floor) of the row's slots, from
@@ -186,6 +201,7 @@ struct RowState {
             ru[q] = pk(j0 < J ? ru_src[j0] : 1.f, j1 < J ? ru_src[j1] : 1.f);
         }
         lam = lam_;
+        il = rcp_refined(lam_);
     }
 
     __device__ __forceinline__ void store_state(float* rh_dst, float* ru_dst) const {
@@ -222,14 +238,15 @@ struct RowState {
     // fixed-order block reduction, pass B per slot.  `parity` selects the half of `red`.
     __device__ __forceinline__ void pass(const RowConst& c, const IterParams& p,
                                          float (*red)[BLOCK / 32 > 0 ? BLOCK / 32 : 1], int parity) {
-        const PassConsts k = pass_consts(c, p, lam);
+        const PassConsts k = pass_consts(c, p, il);
         f32x2 part = dup(0.f);
 #pragma unroll
         for (int q = 0; q < NP; ++q)
             pass_a_pair(k, tr[q], ti[q], sr[q], si[q], kapM[q], q == NP - 1 ? CB_LAST : k.CB, rh[q], ru[q], B[q],
                         part);
         lam = block_sum<BLOCK>(lo_of(part) + hi_of(part), red, parity) * (1.0f / (float)J);
-        const f32x2 ILM = dup(rcp_refined(lam) * c.invM);
+        il = rcp_refined(lam);
+        const f32x2 ILM = dup(il * c.invM);
 #pragma unroll
         for (int q = 0; q < NP; ++q) ru[q] = fma2(B[q], ILM, ru[q]);
     }

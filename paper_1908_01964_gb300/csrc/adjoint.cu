@@ -82,7 +82,7 @@ constexpr int kStage = 2 * kMaxM + 5;                     // x (2M) + g_tau (2) 
 template <int BLOCK, int SPT>
 struct AdjShared {
     float ga_w[2 * kMaxM];   // gradient of a from the Wiener filter (block-uniform)
-    float red[2][BLOCK / 32];
+    __align__(16) float red[2][BLOCK / 32];
     float redn[2][BLOCK / 32][8];
     float2 s_a[kMaxM], s_b[kMaxM], s_Pa[kMaxM], s_P[kMaxM * kMaxM];
     float stage[BLOCK * kStage];

@@ -18,19 +18,67 @@ namespace {
 // as for the plain kernel, need at most 96.
 constexpr int solve_min_blocks(int block, int spt) { return (block == 128 && spt == 8) ? 5 : 0; }
 
-// Shared memory of the fused row body: the row's projection and steering vector.
+// Shared memory of the fused row body: the row's projection and steering vector, and
+// the Wiener weights of its SLOTS slots.
+template <int SLOTS>
 struct FusedSmem {
     float2 phi[kMaxM * kMaxM];
     float2 a[kMaxM];
+    float2 w[SLOTS];
 };
+
+// The fused prologue: invariants of the row's slots j = threadIdx.x + k BLOCK, projected
+// with Phi (shared memory) and stored to the context's arrays.  The prologue and the
+// epilogue run once per row, so their code is fetched cold: a short loop with M fixed for
+// the row (loads of G slots issued together) instead of a body unrolled over the slots
+// with a dispatch on M in each, which took longer to fetch than to run.
+template <int BLOCK, int M>
+__device__ __forceinline__ void project_row(const float2* phi, const float2* x, int J, float4* inv, float* kap) {
+    constexpr int G = M <= 4 ? 4 : 2;
+#pragma unroll 1
+    for (int j0 = threadIdx.x; j0 < J; j0 += G * BLOCK) {
+        float2 xv[G][M];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int j = j0 + g * BLOCK;
+#pragma unroll
+            for (int n = 0; n < M; ++n) xv[g][n] = j < J ? x[(int64_t)j * M + n] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int j = j0 + g * BLOCK;
+            if (j < J) {
+                float4 t;
+                float k;
+                project_vals<M>(phi, xv[g], t, k);
+                inv[j] = t;
+                kap[j] = k;
+            }
+        }
+    }
+}
+
+template <int BLOCK>
+__device__ __forceinline__ void project_row_m(int M, const float2* phi, const float2* x, int J, float4* inv,
+                                              float* kap) {
+    switch (M) {
+        case 2: project_row<BLOCK, 2>(phi, x, J, inv, kap); break;
+        case 3: project_row<BLOCK, 3>(phi, x, J, inv, kap); break;
+        case 4: project_row<BLOCK, 4>(phi, x, J, inv, kap); break;
+        case 5: project_row<BLOCK, 5>(phi, x, J, inv, kap); break;
+        case 6: project_row<BLOCK, 6>(phi, x, J, inv, kap); break;
+        case 7: project_row<BLOCK, 7>(phi, x, J, inv, kap); break;
+        default: project_row<BLOCK, 8>(phi, x, J, inv, kap); break;
+    }
+}
 
 // One row, all n_iter passes with the row held in registers (RowState).
 // FUSED: invariants from x first, Wiener output h last (h != nullptr).
-template <int BLOCK, int NP, bool FUSED>
+template <int BLOCK, int NP, bool FUSED, class FS>
 __device__ __forceinline__ void accel_row(const DevState& d, int r, int J, int64_t off, const RowConst& c,
                                           int n_iter, const IterParams& p,
                                           float (*red)[BLOCK / 32 > 0 ? BLOCK / 32 : 1], float2* __restrict__ h,
-                                          FusedSmem* fs) {
+                                          FS* fs) {
     RowState<BLOCK, NP> st;
     const RowDesc* rd = d.rows + r;
     if constexpr (FUSED) {
@@ -38,12 +86,8 @@ __device__ __forceinline__ void accel_row(const DevState& d, int r, int J, int64
         for (int e = threadIdx.x; e < M * M; e += BLOCK) fs->phi[e] = d.phi[(size_t)r * 64 + e];
         if (threadIdx.x < M) fs->a[threadIdx.x] = d.a32[(size_t)r * kMaxM + threadIdx.x];
         __syncthreads();
-        const float2* x = rd->x;
-        st.load_inv_with(J, c, p, [&](int j, float4& t, float& kap) {
-            project_slot_m(M, fs->phi, x + (int64_t)j * M, t, kap);
-            d.inv4[off + j] = t;
-            d.kap[off + j] = kap;
-        });
+        project_row_m<BLOCK>(M, fs->phi, rd->x, J, d.inv4 + off, d.kap + off);
+        st.load_inv(d, off, J, c, p);                          // this thread's own slots, as just stored
         st.load_state(rd->rh0, rd->ru0, (float)d.lam0[r]);     // the initial state, whatever ran before
     } else {
         st.load_inv(d, off, J, c, p);
@@ -69,27 +113,40 @@ __device__ __forceinline__ void accel_row(const DevState& d, int r, int J, int64
     if constexpr (FUSED) {                           // h = w a with the final state
         const int M = rd->M;
         const float2 sab = make_float2(c.sab_re, c.sab_im);
-        float2* hrow = h + rd->out_off;
 #pragma unroll
-        for (int k = 0; k < 2 * NP; ++k) {
+        for (int k = 0; k < 2 * NP; ++k) {           // the weights of this thread's slots
             const int j = k * BLOCK + threadIdx.x;
             if (j < J) {
                 const float4 t = make_float4(k & 1 ? hi_of(st.tr[k >> 1]) : lo_of(st.tr[k >> 1]),
                                              k & 1 ? hi_of(st.ti[k >> 1]) : lo_of(st.ti[k >> 1]),
                                              k & 1 ? hi_of(st.sr[k >> 1]) : lo_of(st.sr[k >> 1]),
                                              k & 1 ? hi_of(st.si[k >> 1]) : lo_of(st.si[k >> 1]));
-                const float2 w = wiener_weight(c.taa, c.sab2, sab, st.lam, t, st.rh_of(k), st.ru_of(k));
-                float2* hj = hrow + (int64_t)j * M;
-                for (int m = 0; m < M; ++m) hj[m] = cmul_exact(w, fs->a[m]);
+                fs->w[j] = wiener_weight(c.taa, c.sab2, sab, st.lam, t, st.rh_of(k), st.ru_of(k));
+            }
+        }
+        __syncthreads();
+        // the row's J x M outputs are contiguous: entry e = j M + m, consecutive threads on
+        // consecutive entries (coalesced stores)
+        float2* hrow = h + rd->out_off;
+        const int n_out = J * M, dj = BLOCK / M, dm = BLOCK - (BLOCK / M) * M;
+        int j = threadIdx.x / M, m = threadIdx.x - (threadIdx.x / M) * M;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < n_out; e += BLOCK) {
+            hrow[e] = cmul_exact(fs->w[j], fs->a[m]);
+            j += dj;
+            m += dm;
+            if (m >= M) {
+                m -= M;
+                ++j;
             }
         }
     }
 }
 
-template <int BLOCK, int SPT, bool FUSED>
+template <int BLOCK, int SPT, bool FUSED, class FS>
 __device__ __forceinline__ void accel_one_row(const DevState& d, int r, int n_iter, const IterParams& p,
                                               float (*red)[BLOCK / 32 > 0 ? BLOCK / 32 : 1], float2* h,
-                                              FusedSmem* fs) {
+                                              FS* fs) {
     const RowDesc* rd = d.rows + r;
     const int J = rd->J;
     const int64_t off = rd->slot_off;
@@ -98,7 +155,7 @@ __device__ __forceinline__ void accel_one_row(const DevState& d, int r, int n_it
     // The row's exact pair count selects the unrolled body (block-uniform branch).
 #define RCSCM_ROW(N) \
     case N:          \
-        if constexpr (2 * N <= SPT) accel_row<BLOCK, N, FUSED>(d, r, J, off, c, n_iter, p, red, h, fs); \
+        if constexpr (2 * N <= SPT) accel_row<BLOCK, N, FUSED, FS>(d, r, J, off, c, n_iter, p, red, h, fs); \
         break;
     switch (np) {
         RCSCM_ROW(1) RCSCM_ROW(2) RCSCM_ROW(3) RCSCM_ROW(4) RCSCM_ROW(5) RCSCM_ROW(6) RCSCM_ROW(7) RCSCM_ROW(8)
@@ -110,9 +167,10 @@ __device__ __forceinline__ void accel_one_row(const DevState& d, int r, int n_it
 // One CTA per row, rows in the order table (longest first).
 template <int BLOCK, int SPT>
 __global__ void __launch_bounds__(BLOCK) accel_kernel(DevState d, int n_iter, IterParams p) {
-    __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
+    __shared__ __align__(16) float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
     RCSCM_CTA_CHECK(row_ok(d, d.order[blockIdx.x], BLOCK * SPT), d.status);
-    accel_one_row<BLOCK, SPT, false>(d, d.order[blockIdx.x], n_iter, p, red, nullptr, nullptr);
+    accel_one_row<BLOCK, SPT, false>(d, d.order[blockIdx.x], n_iter, p, red, nullptr,
+                                     static_cast<FusedSmem<1>*>(nullptr));
 }
 
 // Launched as a programmatic dependent of the per-frequency setup: a CTA may start while
@@ -121,8 +179,8 @@ __global__ void __launch_bounds__(BLOCK) accel_kernel(DevState d, int n_iter, It
 // writes them is still seen); every setup output is read after the wait.
 template <int BLOCK, int SPT>
 __global__ void __launch_bounds__(BLOCK, solve_min_blocks(BLOCK, SPT)) solve_kernel(DevState d, int n_iter, IterParams p, float2* h) {
-    __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
-    __shared__ FusedSmem fs;
+    __shared__ __align__(16) float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
+    __shared__ FusedSmem<BLOCK * SPT> fs;
     const int r = d.order[blockIdx.x];
     RCSCM_CTA_CHECK(row_ok(d, r, BLOCK * SPT), d.status);
     {
@@ -147,7 +205,7 @@ __global__ void __launch_bounds__(BLOCK, solve_min_blocks(BLOCK, SPT)) solve_ker
 // table through an atomic counter (dynamic longest-first scheduling).
 template <int BLOCK, int SPT>
 __global__ void __launch_bounds__(BLOCK) accel_persistent_kernel(DevState d, int n_iter, IterParams p, int n_rows) {
-    __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
+    __shared__ __align__(16) float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
     __shared__ int s_next;
     for (;;) {
         __syncthreads();                    // every thread is done with s_next and the previous row
@@ -156,15 +214,15 @@ __global__ void __launch_bounds__(BLOCK) accel_persistent_kernel(DevState d, int
         const int k = s_next;
         if (k >= n_rows) break;
         RCSCM_CTA_CHECK(row_ok(d, d.order[k], BLOCK * SPT), d.status);
-        accel_one_row<BLOCK, SPT, false>(d, d.order[k], n_iter, p, red, nullptr, nullptr);
+        accel_one_row<BLOCK, SPT, false>(d, d.order[k], n_iter, p, red, nullptr, static_cast<FusedSmem<1>*>(nullptr));
     }
 }
 
 template <int BLOCK, int SPT>
 __global__ void __launch_bounds__(BLOCK, solve_min_blocks(BLOCK, SPT)) solve_persistent_kernel(DevState d, int n_iter, IterParams p, int n_rows,
                                                                  float2* h) {
-    __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
-    __shared__ FusedSmem fs;
+    __shared__ __align__(16) float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
+    __shared__ FusedSmem<BLOCK * SPT> fs;
     __shared__ int s_next;
     for (;;) {
         __syncthreads();                    // every thread is done with s_next, fs and the previous row

@@ -199,11 +199,8 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // row 0 gives tau_ax, row M-1 sigma_bx, rows 1..M-2 the components whose squared
 // norm is kappa = tau_xx - |tau_ax|^2 / tau_aa).  out = {tau_ax, sigma_bx}.
 template <int M>
-__device__ __forceinline__ void project_slot(const float2* __restrict__ phi, const float2* __restrict__ xs,
-                                             float4& out, float& kappa) {
-    float2 xv[M];
-#pragma unroll
-    for (int n = 0; n < M; ++n) xv[n] = xs[n];
+__device__ __forceinline__ void project_vals(const float2* __restrict__ phi, const float2 (&xv)[M], float4& out,
+                                             float& kappa) {
     float2 z0 = make_float2(0.f, 0.f), zb = make_float2(0.f, 0.f);
 #pragma unroll
     for (int n = 0; n < M; ++n) {
@@ -220,6 +217,14 @@ __device__ __forceinline__ void project_slot(const float2* __restrict__ phi, con
     }
     out = make_float4(z0.x, z0.y, zb.x, zb.y);
     kappa = kap;
+}
+template <int M>
+__device__ __forceinline__ void project_slot(const float2* __restrict__ phi, const float2* __restrict__ xs,
+                                             float4& out, float& kappa) {
+    float2 xv[M];
+#pragma unroll
+    for (int n = 0; n < M; ++n) xv[n] = xs[n];
+    project_vals<M>(phi, xv, out, kappa);
 }
 
 // Projection of one slot for a runtime M (2..8).

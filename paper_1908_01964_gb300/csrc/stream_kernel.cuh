@@ -17,7 +17,7 @@ struct PairIn {
 
 template <int BLOCK, int SPT>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) accel_stream_kernel(DevState d, IterParams p) {
-    __shared__ float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
+    __shared__ __align__(16) float red[2][BLOCK / 32 > 0 ? BLOCK / 32 : 1];
     __shared__ f32x2 s_am[SPT / 2][BLOCK], s_b[SPT / 2][BLOCK];
     const int r = d.order[blockIdx.x];
     RCSCM_CTA_CHECK(row_ok(d, r, BLOCK * SPT), d.status);
@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) accel_stream_kernel(DevSt
     const float lam0 = d.lam[r];
     const bool ckpt = d.ckpt_stride > 0 && p.ckpt_first % d.ckpt_stride == 0;
     const size_t kc = ckpt ? (size_t)(p.ckpt_first / d.ckpt_stride) : 0;
-    const PassConsts k = pass_consts(c, p, lam0);
+    const PassConsts k = pass_consts(c, p, rcp_refined(lam0));
     // loads of pair q (padding: zero invariants, r_h = 0, r_u = 1, kappa/M = 1)
     auto load_pair = [&](int q) {
         PairIn in;
