@@ -77,7 +77,9 @@ __device__ __forceinline__ void pair_add(float& hi, float& lo, float hi2, float 
     lo = e - (hi - s);
 }
 
-constexpr int kStage = 2 * kMaxM + 5;                     // x (2M) + g_tau (2) + g_sigma (2) + g_txx
+// staged slot record: x (2 kMaxM), g_tau (2), g_sigma (2), g_txx, 1
+constexpr int kGtau = 2 * kMaxM, kGsig = 2 * kMaxM + 2, kGtxx = 2 * kMaxM + 4, kOne = 2 * kMaxM + 5;
+constexpr int kStage = 2 * kMaxM + 6;
 
 template <int BLOCK, int SPT>
 struct AdjShared {
@@ -186,12 +188,15 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
             const float2 w = cscale(rax, kk);
             const float2* gh = g.grad_h + rd->out_off + (int64_t)j * M;
             float2 gw = make_float2(0.f, 0.f);
-            for (int m = 0; m < M; ++m) {
-                const float2 ghm = gh[m];
-                gw = cfma(ghm, cconj(s_a[m]), gw);               // g_w = sum_m g_h conj(a)
-                const float2 t = cmul(ghm, cconj(w));             // g_a += g_h conj(w)
-                pw[4 + 2 * m] += t.x;
-                pw[5 + 2 * m] += t.y;
+#pragma unroll
+            for (int m = 0; m < kMaxM; ++m) {
+                if (m < M) {
+                    const float2 ghm = gh[m];
+                    gw = cfma(ghm, cconj(s_a[m]), gw);               // g_w = sum_m g_h conj(a)
+                    const float2 t = cmul(ghm, cconj(w));             // g_a += g_h conj(w)
+                    pw[4 + 2 * m] += t.x;
+                    pw[5 + 2 * m] += t.y;
+                }
             }
             const float gk = gw.x * rax.x + gw.y * rax.y;          // Re(conj(g_w) rax)
             const float2 grax = cscale(gw, kk);
@@ -390,67 +395,100 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     // sm_103a FP64 runs at a small fraction of the FP32 rate).  Each role's slots are
     // split over n_groups threads (contiguous slot ranges of every staged block); their
     // partials are combined per role in group order as error-free FP32 pairs.
-    float2 acc = make_float2(0.f, 0.f), comp = make_float2(0.f, 0.f);
     const int n_roles = MM + 2 * M;
     const int n_groups = BLOCK / n_roles > 1 ? BLOCK / n_roles : 1;
     const int role = tid % n_roles, grp = tid / n_roles;
     const int span = (BLOCK + n_groups - 1) / n_groups;
-    for (int k = 0; k < NK; ++k) {
+    // Every role's term has one form, (o[ia] + i o[ia+1]) conj(o[ib] + i o[ib+1]) o[is] of a
+    // staged record o (C_mn: x_m conj(x_n) g_txx; v_a: x_m conj(g_tau) 1; v_b: x_m conj(g_sigma) 1),
+    // so the warps do not diverge; the record offsets are formed once (no division per term).
+    int ia, ib, is;
+    if (role < MM) {
+        ia = 2 * (role / M);
+        ib = 2 * (role % M);
+        is = kGtxx;
+    } else {
+        ia = 2 * ((role - MM) % M);
+        ib = role < MM + M ? kGtau : kGsig;
+        is = kOne;
+    }
+    // four interleaved compensated sums per thread (independent chains), combined at the end
+    float2 acc[4], comp[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = comp[u] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {                  // unrolled: the per-slot arrays stay in registers
         const int j = k * BLOCK + tid;
         float* my = stage + tid * kStage;
         if (valid[k]) {
             const float2* xj = rd->x + (int64_t)j * M;
             float2 xv[kMaxM];
-            for (int m = 0; m < M; ++m) xv[m] = xj[m];
+#pragma unroll
+            for (int m = 0; m < kMaxM; ++m) xv[m] = m < M ? xj[m] : make_float2(0.f, 0.f);
             const float gtxx = g_k[k];
             const float gtr = g_tr[k] - 2.f * tr[k] * gtxx * c.inv_taa;
             const float gti = g_ti[k] - 2.f * ti[k] * gtxx * c.inv_taa;
             p_taa += gtxx * (tr[k] * tr[k] + ti[k] * ti[k]) * c.inv_taa * c.inv_taa;
             const float2 gt = make_float2(gtr, gti), gs = make_float2(g_sr[k], g_si[k]);
             float2* gx = g.grad_x + rd->out_off + (int64_t)j * M;
-            for (int m = 0; m < M; ++m) {
-                float2 px = make_float2(0.f, 0.f);
-                for (int n = 0; n < M; ++n) px = cfma(s_P[m * M + n], xv[n], px);
-                float2 v = cmul(s_Pa[m], gt);                 // g_x = P a g_tau + b g_sigma + 2 g_txx P x
-                v = cfma(s_b[m], gs, v);
-                v = cadd(v, cscale(px, 2.f * gtxx));
-                gx[m] = v;
-                my[2 * m] = xv[m].x;
-                my[2 * m + 1] = xv[m].y;
+#pragma unroll
+            for (int m = 0; m < kMaxM; ++m) {
+                if (m < M) {
+                    float2 px = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int n = 0; n < kMaxM; ++n)
+                        if (n < M) px = cfma(s_P[m * M + n], xv[n], px);
+                    float2 v = cmul(s_Pa[m], gt);             // g_x = P a g_tau + b g_sigma + 2 g_txx P x
+                    v = cfma(s_b[m], gs, v);
+                    v = cadd(v, cscale(px, 2.f * gtxx));
+                    gx[m] = v;
+                    my[2 * m] = xv[m].x;
+                    my[2 * m + 1] = xv[m].y;
+                }
             }
-            my[2 * kMaxM] = gtr;
-            my[2 * kMaxM + 1] = gti;
-            my[2 * kMaxM + 2] = gs.x;
-            my[2 * kMaxM + 3] = gs.y;
-            my[2 * kMaxM + 4] = gtxx;
+            my[kGtau] = gtr;
+            my[kGtau + 1] = gti;
+            my[kGsig] = gs.x;
+            my[kGsig + 1] = gs.y;
+            my[kGtxx] = gtxx;
+            my[kOne] = 1.f;
         } else {
             for (int i = 0; i < kStage; ++i) my[i] = 0.f;
         }
         __syncthreads();
         if (grp < n_groups) {
-            const int sl1 = min(BLOCK, (grp + 1) * span);
-            for (int sl = grp * span; sl < sl1; ++sl) {
+            const int sl0 = grp * span, sl1 = min(BLOCK, sl0 + span);
+            auto term_at = [&](int sl) {
                 const float* o = stage + sl * kStage;
-                float2 term;
-                if (role < MM) {
-                    const int m = role / M, n = role % M;
-                    const float2 xm = make_float2(o[2 * m], o[2 * m + 1]), xn = make_float2(o[2 * n], o[2 * n + 1]);
-                    term = cscale(cmul(xm, cconj(xn)), o[2 * kMaxM + 4]);
-                } else {
-                    const int m = (role - MM) % M;
-                    const int q = role < MM + M ? 0 : 2;               // g_tau or g_sigma
-                    term = cmul(make_float2(o[2 * m], o[2 * m + 1]),
-                                make_float2(o[2 * kMaxM + q], -o[2 * kMaxM + q + 1]));
+                return cscale(cmul(make_float2(o[ia], o[ia + 1]), make_float2(o[ib], -o[ib + 1])), o[is]);
+            };
+            int sl = sl0;
+            for (; sl + 4 <= sl1; sl += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 t = term_at(sl + u);
+                    kahan_add(acc[u].x, comp[u].x, t.x);
+                    kahan_add(acc[u].y, comp[u].y, t.y);
                 }
-                kahan_add(acc.x, comp.x, term.x);
-                kahan_add(acc.y, comp.y, term.y);
+            }
+            for (int u = 0; sl < sl1; ++sl, ++u) {
+                const float2 t = term_at(sl);
+                kahan_add(acc[u].x, comp[u].x, t.x);
+                kahan_add(acc[u].y, comp[u].y, t.y);
             }
         }
         __syncthreads();
     }
-    // the groups' partials of each role, combined in group order (stage is free again)
+    // this thread's four sums as one error-free pair each for re and im, then the groups'
+    // partials of each role, combined in group order (stage is free again)
+    float4 mine = make_float4(acc[0].x, -comp[0].x, acc[0].y, -comp[0].y);
+#pragma unroll
+    for (int u = 1; u < 4; ++u) {
+        pair_add(mine.x, mine.y, acc[u].x, -comp[u].x);
+        pair_add(mine.z, mine.w, acc[u].y, -comp[u].y);
+    }
     float4* part = reinterpret_cast<float4*>(stage);
-    if (grp < n_groups) part[grp * n_roles + role] = make_float4(acc.x, -comp.x, acc.y, -comp.y);
+    if (grp < n_groups) part[grp * n_roles + role] = mine;
     // row-constant partials
     float pv[8] = {p_taa, p_taaM, p_invtaa, p_sab2, p_sre, p_sim, 0.f, 0.f};
     block_sum_n<BLOCK, 8>(pv, redn, (parity++) & 1);        // its barrier also publishes `part`
@@ -501,17 +539,21 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
         dT[m][n] = zscale(zadd(zadd(dG[m][n], t1), zconj(zadd(dG[n][m], t2))), 0.5);
     }
     __syncwarp();
-    double2 tmp[2];
-    int cnt = 0;
-    for (int e = lane; e < MM; e += 32, ++cnt) {            // G E
-        const int m = e / M, n = e % M;
-        double2 v = make_double2(0.0, 0.0);
-        for (int k = 0; k < M; ++k) v = zfma(v, dT[m][k], dE[k][n]);
-        tmp[cnt] = v;
+    double2 tmp[2];                                           // M * M <= 64: two entries per lane
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {                             // G E
+        const int e = lane + 32 * t;
+        if (e < MM) {
+            const int m = e / M, n = e % M;
+            double2 v = make_double2(0.0, 0.0);
+            for (int k = 0; k < M; ++k) v = zfma(v, dT[m][k], dE[k][n]);
+            tmp[t] = v;
+        }
     }
     __syncwarp();
-    cnt = 0;
-    for (int e = lane; e < MM; e += 32, ++cnt) dG[e / M][e % M] = tmp[cnt];
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+        if (lane + 32 * t < MM) dG[(lane + 32 * t) / M][(lane + 32 * t) % M] = tmp[t];
     __syncwarp();
     for (int e = lane; e < MM; e += 32) {                     // G' = E^H (G E)
         const int i = e / M, k = e % M;
