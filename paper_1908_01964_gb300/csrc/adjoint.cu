@@ -88,9 +88,7 @@ struct AdjShared {
     float redn[2][BLOCK / 32][8];
     float2 s_a[kMaxM], s_b[kMaxM], s_Pa[kMaxM], s_P[kMaxM * kMaxM];
     float stage[BLOCK * kStage];
-    double2 dP[kMaxM][kMaxM], dG[kMaxM][kMaxM], dT[kMaxM][kMaxM];
-    double2 dva[kMaxM], dvb[kMaxM], dga[kMaxM], dgb[kMaxM], dGb[kMaxM];
-    double2 dA_[kMaxM], dE[kMaxM][kMaxM];
+    double2 dP[kMaxM][kMaxM], dE[kMaxM][kMaxM];
     double dmu[kMaxM], dimu[kMaxM];
 };
 
@@ -106,9 +104,6 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     float2* s_P = sh.s_P;
     float* stage = sh.stage;
     double2(*dP)[kMaxM] = sh.dP;
-    double2(*dG)[kMaxM] = sh.dG;
-    double2(*dT)[kMaxM] = sh.dT;
-    double2 *dva = sh.dva, *dvb = sh.dvb, *dga = sh.dga, *dgb = sh.dgb, *dGb = sh.dGb, *dA_ = sh.dA_;
     double2(*dE)[kMaxM] = sh.dE;
     double* dmu = sh.dmu;
     double* dimu = sh.dimu;
@@ -120,6 +115,15 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     const RowConst c = d.rc[r];
     const int tid = threadIdx.x;
     const int MM = M * M;
+    {   // the row's upstream gradient (read by step 1) and x (step 3), asked of L2 now
+        const int64_t bytes = (int64_t)J * M * (int64_t)sizeof(float2);
+        const char* ghb = reinterpret_cast<const char*>(g.grad_h + rd->out_off);
+        const char* xb = reinterpret_cast<const char*>(rd->x);
+        for (int64_t o = (int64_t)tid * 128; o < bytes; o += (int64_t)BLOCK * 128) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ghb + o));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(xb + o));
+        }
+    }
     if (tid < M) {
         s_a[tid] = d.a32[(size_t)r * kMaxM + tid];
         s_b[tid] = d.b32[(size_t)r * kMaxM + tid];
@@ -500,22 +504,82 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
             pair_add(tot.z, tot.w, q.z, q.w);
         }
 
-    // ---- 4. setup adjoint in FP64 (warp 0) -----------------------------------------------
-    const double2 accd = make_double2((double)tot.x + (double)tot.y, (double)tot.z + (double)tot.w);
-    if (tid < MM) dG[tid / M][tid % M] = accd;
-    else if (tid < MM + M) dva[tid - MM] = accd;
-    else if (tid < n_roles) dvb[tid - MM - M] = accd;
-    __syncthreads();
-    if (tid >= 32) return;
-    const int lane = tid;
-    const double taa = d.taa64[r];
-    const double2 sab = d.sab64[r];
-    if (lane < M) dA_[lane] = rd->a[lane];
+    // ---- 4. the row's sums, for the setup adjoint (adjoint_setup_kernel) ------------------------
+    // role sums in FP64 (the FP32 pairs added once), the total adjoints of tau_aa and sigma_ab
+    // (FP64 from the FP32 sums) and the Wiener filter's gradient of a
+    double* out = g.sums + (size_t)r * kAdjSums;
+    if (tid < n_roles) {
+        out[2 * tid] = (double)tot.x + (double)tot.y;
+        out[2 * tid + 1] = (double)tot.z + (double)tot.w;
+    }
+    if (tid == 0) {
+        const double taa = d.taa64[r];
+        const double2 sab = d.sab64[r];
+        out[kAdjGtaa] = (double)u_taa + (double)pv[0] + (double)pv[1] / M - (double)pv[2] / (taa * taa);
+        out[kAdjGsab] = (double)u_sre + pv[4] + 2.0 * sab.x * ((double)u_sab2 + pv[3]);
+        out[kAdjGsab + 1] = (double)u_sim + pv[5] + 2.0 * sab.y * ((double)u_sab2 + pv[3]);
+        for (int i = 0; i < 2 * kMaxM; ++i) out[kAdjGaw + i] = (double)sh.ga_w[i];
+    }
+}
+
+// Step 4, the setup adjoint in FP64, one row per warp (lanes own matrix entries): from the
+// row kernel's sums it forms g_a and the gradient of R' through the eigenpairs of R'.  As
+// its own kernel it runs many rows per SM at once, instead of holding a row kernel's CTA
+// with one FP64 warp.
+struct SetupAdjShared {
+    double2 dP[kMaxM][kMaxM], dG[kMaxM][kMaxM], dT[kMaxM][kMaxM];
+    double2 dva[kMaxM], dvb[kMaxM], dga[kMaxM], dgb[kMaxM], dGb[kMaxM];
+    double2 dA_[kMaxM], dE[kMaxM][kMaxM];
+    double dmu[kMaxM], dimu[kMaxM];
+};
+constexpr int kSetupAdjWarps = 4;
+
+// LANES = 16 (M <= 4, two rows per warp) or 32: lanes per row.  A warp's rows run the same
+// instruction stream, so the rows of a launch with M <= 4 take half the FP64 instructions.
+template <int LANES>
+__global__ void __launch_bounds__(kSetupAdjWarps * 32) adjoint_setup_kernel(DevState d, AdjointArgs g, int n_rows) {
+    constexpr int kRowsPerCta = kSetupAdjWarps * 32 / LANES;
+    __shared__ SetupAdjShared shw[kRowsPerCta];
+    const int lane = threadIdx.x & (LANES - 1);
+    SetupAdjShared& sh = shw[threadIdx.x / LANES];
+    const int r0 = blockIdx.x * kRowsPerCta + (int)(threadIdx.x / LANES);
+    const bool active = r0 < n_rows;                          // an idle row keeps its warp's syncs
+    const int r = active ? r0 : n_rows - 1;
+    const RowDesc* rd = d.rows + r;
+    const int M = rd->M;
+    const int MM = M * M;
+    double2(*dP)[kMaxM] = sh.dP;
+    double2(*dG)[kMaxM] = sh.dG;
+    double2(*dT)[kMaxM] = sh.dT;
+    double2 *dva = sh.dva, *dvb = sh.dvb, *dga = sh.dga, *dgb = sh.dgb, *dGb = sh.dGb, *dA_ = sh.dA_;
+    double2(*dE)[kMaxM] = sh.dE;
+    double* dmu = sh.dmu;
+    double* dimu = sh.dimu;
+    const double* in = g.sums + (size_t)r * kAdjSums;
+    if (lane < M) {
+        const double mu = d.mu[(size_t)r * kMaxM + lane];
+        dmu[lane] = mu;
+        dimu[lane] = lane >= 1 ? 1.0 / mu : 0.0;              // 1/mu_i of the nonzero eigenpairs
+        dA_[lane] = rd->a[lane];
+    }
+    for (int e = lane; e < MM; e += LANES) dE[e / M][e % M] = d.evec64[(size_t)r * 64 + e];
+    const int n_roles = MM + 2 * M;
+    for (int t = lane; t < n_roles; t += LANES) {                // C, v_a, v_b of the row kernel
+        const double2 v = make_double2(in[2 * t], in[2 * t + 1]);
+        if (t < MM) dG[t / M][t % M] = v;
+        else if (t < MM + M) dva[t - MM] = v;
+        else dvb[t - MM - M] = v;
+    }
     __syncwarp();
-    // total adjoints of tau_aa and sigma_ab (FP64 from the FP32 sums)
-    const double g_taa = (double)u_taa + (double)pv[0] + (double)pv[1] / M - (double)pv[2] / (taa * taa);
-    const double2 g_sab = make_double2((double)u_sre + pv[4] + 2.0 * sab.x * ((double)u_sab2 + pv[3]),
-                                       (double)u_sim + pv[5] + 2.0 * sab.y * ((double)u_sab2 + pv[3]));
+    for (int e = lane; e < MM; e += LANES) {                     // P = sum_{i>=2} e_i e_i^H / mu_i
+        const int m = e / M, n = e % M;
+        double2 v = make_double2(0.0, 0.0);
+        for (int i = 1; i < M; ++i) v = zadd(v, zscale(zmulc(dE[n][i], dE[m][i]), dimu[i]));
+        dP[m][n] = v;
+    }
+    __syncwarp();
+    const double g_taa = in[kAdjGtaa];
+    const double2 g_sab = make_double2(in[kAdjGsab], in[kAdjGsab + 1]);
     if (lane < M) {
         double2 pa = make_double2(0.0, 0.0), pva = make_double2(0.0, 0.0);
         for (int n = 0; n < M; ++n) {
@@ -523,7 +587,7 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
             pva = zfma(pva, dP[lane][n], dva[n]);
         }
         // g_a = g_a(Wiener) + P v_a + 2 g_taa P a + b conj(g_sab)
-        double2 ga = make_double2((double)sh.ga_w[2 * lane], (double)sh.ga_w[2 * lane + 1]);
+        double2 ga = make_double2(in[kAdjGaw + 2 * lane], in[kAdjGaw + 2 * lane + 1]);
         ga = zadd(ga, pva);
         ga = zadd(ga, zscale(pa, 2.0 * g_taa));
         ga = zadd(ga, zmul(dE[lane][0], zconj(g_sab)));
@@ -532,17 +596,18 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     }
     __syncwarp();
     // G = Hermitian part of (C + g_taa a a^H + a v_a^H)
-    for (int e = lane; e < MM; e += 32) {
+    for (int e = lane; e < MM; e += LANES) {
         const int m = e / M, n = e % M;
         const double2 t1 = zadd(zscale(zmul(dA_[m], zconj(dA_[n])), g_taa), zmul(dA_[m], zconj(dva[n])));
         const double2 t2 = zadd(zscale(zmul(dA_[n], zconj(dA_[m])), g_taa), zmul(dA_[n], zconj(dva[m])));
         dT[m][n] = zscale(zadd(zadd(dG[m][n], t1), zconj(zadd(dG[n][m], t2))), 0.5);
     }
     __syncwarp();
-    double2 tmp[2];                                           // M * M <= 64: two entries per lane
+    constexpr int kPer = (kMaxM * kMaxM + LANES - 1) / LANES;
+    double2 tmp[kPer];                                        // at most kPer entries per lane
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {                             // G E
-        const int e = lane + 32 * t;
+    for (int t = 0; t < kPer; ++t) {                          // G E
+        const int e = lane + LANES * t;
         if (e < MM) {
             const int m = e / M, n = e % M;
             double2 v = make_double2(0.0, 0.0);
@@ -552,10 +617,10 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     }
     __syncwarp();
 #pragma unroll
-    for (int t = 0; t < 2; ++t)
-        if (lane + 32 * t < MM) dG[(lane + 32 * t) / M][(lane + 32 * t) % M] = tmp[t];
+    for (int t = 0; t < kPer; ++t)
+        if (lane + LANES * t < MM) dG[(lane + LANES * t) / M][(lane + LANES * t) % M] = tmp[t];
     __syncwarp();
-    for (int e = lane; e < MM; e += 32) {                     // G' = E^H (G E)
+    for (int e = lane; e < MM; e += LANES) {                     // G' = E^H (G E)
         const int i = e / M, k = e % M;
         double2 v = make_double2(0.0, 0.0);
         for (int m = 0; m < M; ++m) v = zfma_c(v, dE[m][i], dG[m][k]);
@@ -568,7 +633,7 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     }
     __syncwarp();
     const double mu1 = dmu[0];
-    for (int e = lane; e < MM; e += 32) {                     // F (eigenbasis)
+    for (int e = lane; e < MM; e += LANES) {                     // F (eigenbasis)
         const int i = e / M, k = e % M;
         double2 f = make_double2(0.0, 0.0);
         if (i >= 1 && k >= 1) {
@@ -582,7 +647,7 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
         dG[i][k] = f;
     }
     __syncwarp();
-    for (int e = lane; e < MM; e += 32) {                     // F E^H
+    for (int e = lane; e < MM; e += LANES) {                     // F E^H
         const int i = e / M, n = e % M;
         double2 v = make_double2(0.0, 0.0);
         for (int k = 0; k < M; ++k) v = zfma(v, dG[i][k], zconj(dE[n][k]));
@@ -590,14 +655,15 @@ __device__ __forceinline__ void adjoint_row(const DevState& d, const AdjointArgs
     }
     __syncwarp();
     double2* gR = g.grad_Rp + rd->rp_off;
-    for (int e = lane; e < MM; e += 32) {                     // E (F E^H)
+    for (int e = lane; e < MM && active; e += LANES) {           // E (F E^H)
         const int m = e / M, n = e % M;
         double2 v = make_double2(0.0, 0.0);
         for (int i = 0; i < M; ++i) v = zfma(v, dE[m][i], dT[i][n]);
         gR[e] = v;
     }
-    if (lane < M) g.grad_a[rd->a_off + lane] = dga[lane];
+    if (active && lane < M) g.grad_a[rd->a_off + lane] = dga[lane];
 }
+
 
 // One CTA per row; the row's exact count of chunk pairs selects the body (as in the
 // forward kernel, so the recomputed states equal the forward ones bit for bit).
@@ -623,7 +689,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 128 ? 4 : 1) adjoint_kernel(De
 // The segment buffer goes to shared memory when it fits beside the kernel's static shared
 // memory within the per-block limit (and leaves room for the CTAs the registers allow).
 template <int BLOCK, int SPT>
-cudaError_t launch_adjoint_t(const DevState& d, int n_rows, const AdjointArgs& a, const IterParams& p,
+cudaError_t launch_adjoint_t(const DevState& d, int n_rows, int max_m, const AdjointArgs& a, const IterParams& p,
                              cudaStream_t s) {
     const size_t bytes = ((size_t)2 * a.stride * SPT * BLOCK + (size_t)a.stride) * sizeof(float);
     static size_t limit = 0;
@@ -648,6 +714,14 @@ cudaError_t launch_adjoint_t(const DevState& d, int n_rows, const AdjointArgs& a
     }
     const bool in_smem = bytes <= 96 * 1024 && bytes <= limit;
     adjoint_kernel<BLOCK, SPT><<<n_rows, BLOCK, in_smem ? bytes : 0, s>>>(d, a, p, in_smem ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (max_m <= 4)
+        adjoint_setup_kernel<16><<<(n_rows + 2 * kSetupAdjWarps - 1) / (2 * kSetupAdjWarps), kSetupAdjWarps * 32, 0, s>>>(
+            d, a, n_rows);
+    else
+        adjoint_setup_kernel<32><<<(n_rows + kSetupAdjWarps - 1) / kSetupAdjWarps, kSetupAdjWarps * 32, 0, s>>>(d, a,
+                                                                                                         n_rows);
     return cudaGetLastError();
 }
 
@@ -655,12 +729,12 @@ cudaError_t launch_adjoint_t(const DevState& d, int n_rows, const AdjointArgs& a
 
 // Shapes (threads per row, slots per thread) follow the forward kernel's: the
 // block of a context with checkpoints is adjoint_block(max_j).
-cudaError_t launch_adjoint(const DevState& d, int n_rows, int max_j, int block, const AdjointArgs& a,
+cudaError_t launch_adjoint(const DevState& d, int n_rows, int max_j, int max_m, int block, const AdjointArgs& a,
                            const IterParams& p, cudaStream_t s) {
     const int need = (max_j + block - 1) / block;
-    if (block == 128 && need <= 4) return launch_adjoint_t<128, 4>(d, n_rows, a, p, s);
-    if (block == 256 && need <= 4) return launch_adjoint_t<256, 4>(d, n_rows, a, p, s);
-    if (block == 256 && need <= 8) return launch_adjoint_t<256, 8>(d, n_rows, a, p, s);
+    if (block == 128 && need <= 4) return launch_adjoint_t<128, 4>(d, n_rows, max_m, a, p, s);
+    if (block == 256 && need <= 4) return launch_adjoint_t<256, 4>(d, n_rows, max_m, a, p, s);
+    if (block == 256 && need <= 8) return launch_adjoint_t<256, 8>(d, n_rows, max_m, a, p, s);
     return cudaErrorInvalidValue;
 }
 

@@ -43,6 +43,7 @@ struct rcscm_ctx {
     float* seg_rh = nullptr;         // adjoint scratch: [stride][S], [stride][S], [stride][R]
     float* seg_ru = nullptr;
     float* seg_lam = nullptr;
+    double* adj_sums = nullptr;      // [R][kAdjSums] row sums handed to the setup adjoint
     int* ident = nullptr;            // rows 0..R-1 in order (row ranges of the fused kernel)
     int iters_done = 0;              // passes since the last setup / set_state
     int iter_block = 0;              // block of those passes (-1: mixed)
@@ -367,6 +368,7 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
         if (!st) st = dalloc(c, &c->seg_rh, Sz * seg);
         if (!st) st = dalloc(c, &c->seg_ru, Sz * seg);
         if (!st) st = dalloc(c, &c->seg_lam, Rz * seg);
+        if (!st) st = dalloc(c, &c->adj_sums, Rz * kAdjSums);
     }
     if (!st && opt->rule == RCSCM_RULE_NAIVE) {            // two values per slot
         float* q = nullptr;
@@ -738,11 +740,12 @@ int rcscm_backward(rcscm_ctx* c, const void* grad_h, void* grad_x, void* grad_a,
     g.seg_rh = c->seg_rh;
     g.seg_ru = c->seg_ru;
     g.seg_lam = c->seg_lam;
+    g.sums = c->adj_sums;
     g.K = c->iters_done;
     g.stride = c->opt.ckpt_stride;
     g.S = c->S;
     g.R = c->R;
-    return map_cuda(launch_adjoint(c->d, (int)c->R, c->max_j, c->opt.block, g, iter_params(c->opt),
+    return map_cuda(launch_adjoint(c->d, (int)c->R, c->max_j, c->max_m, c->opt.block, g, iter_params(c->opt),
                                    static_cast<cudaStream_t>(stream)));
 }
 

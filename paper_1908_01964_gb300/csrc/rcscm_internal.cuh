@@ -290,6 +290,14 @@ inline int accel_max_j(int block) { return block ? block * accel_max_spt(block) 
 // checkpoints): 128 threads for rows up to 512 frames, 256 up to 2048; 0 beyond.
 inline int adjoint_block(int max_j) { return max_j <= 512 ? 128 : (max_j <= 2048 ? 256 : 0); }
 
+// Per-row record handed from the adjoint's row kernel to its setup-adjoint kernel (doubles):
+// the role sums C (M*M), v_a (M), v_b (M) as (re, im) pairs, then g_tau_aa, g_sigma_ab (re, im)
+// and the Wiener filter's gradient of a (2 kMaxM).
+constexpr int kAdjGtaa = 2 * (rcscm::kMaxM * rcscm::kMaxM + 2 * rcscm::kMaxM);
+constexpr int kAdjGsab = kAdjGtaa + 1;
+constexpr int kAdjGaw = kAdjGsab + 2;
+constexpr int kAdjSums = kAdjGaw + 2 * rcscm::kMaxM;
+
 struct AdjointArgs {
     const float2* grad_h;   // upstream gradient of h (concatenated, like h_out)
     float2* grad_x;         // like x, concatenated
@@ -301,6 +309,7 @@ struct AdjointArgs {
     float* seg_rh;          // [stride][S] states entering the passes of one segment (scratch)
     float* seg_ru;          // [stride][S]
     float* seg_lam;         // [stride][R]
+    double* sums;           // [R][kAdjSums] each row's sums for the setup adjoint (scratch)
     int K;                  // passes run since setup
     int stride;             // passes between checkpoints
     int64_t S, R;
@@ -347,6 +356,6 @@ int accel1_block(int max_j);
 // rows_by_m / count_by_m / first_by_m as for launch_naive.
 cudaError_t launch_accel1(const DevState& d, const int* rows_by_m, const int* count_by_m, const int* first_by_m,
                           int max_j, int n_iter, const IterParams& p, cudaStream_t s);
-cudaError_t launch_adjoint(const DevState& d, int n_rows, int max_j, int block, const AdjointArgs& a,
+cudaError_t launch_adjoint(const DevState& d, int n_rows, int max_j, int max_m, int block, const AdjointArgs& a,
                            const IterParams& p, cudaStream_t s);
 }  // namespace rcscm
