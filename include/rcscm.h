@@ -136,7 +136,9 @@ typedef struct {
     int    ckpt_max_iters;   /* with ckpt_stride > 0: most passes that may run between
                                 two rcscm_setup / rcscm_set_state calls; sizes the
                                 checkpoint memory, ceil(ckpt_max_iters / ckpt_stride)
-                                states of 8 B per slot                                   */
+                                states of 8 B per slot (plus the adjoint's scratch:
+                                min(ckpt_stride, ckpt_max_iters) states, and 1.4 KB per
+                                frequency row)                                           */
 } rcscm_options;
 
 /* Fill *opt with the defaults listed above. */

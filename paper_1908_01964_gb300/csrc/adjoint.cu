@@ -18,9 +18,10 @@
 //      tau_xx = x^H P x, sigma_bx = b^H x with P = (R')^+ (Eq. (eq:riinv)):
 //      g_x = P a g_tau + 2 g_txx P x + b g_sigma per slot, and the row sums
 //      v_a = sum_j x_j conj(g_tau_j), v_b = sum_j x_j conj(g_sigma_j),
-//      C = sum_j g_txx_j x_j x_j^H, staged through shared memory and added in
-//      slot order with compensated FP32 sums.
-//   4. Setup (FP64, warp 0, entry-parallel), in the eigenbasis E of R' (mu_1 <
+//      C = sum_j g_txx_j x_j x_j^H, staged through shared memory and added with
+//      compensated FP32 sums (four interleaved per thread, joined as error-free pairs).
+//   4. Setup (FP64, adjoint_setup_kernel: a group of 16 or 32 lanes per row, entry-
+//      parallel, from a per-row record of the row kernel's sums), in the eigenbasis E of R' (mu_1 <
 //      mu_2 <= ...; b = e_1; P = sum_{i>=2} e_i e_i^H / mu_i).  With G the
 //      Hermitian gradient of P and g_b that of b (every use: tau_aa = a^H P a,
 //      sigma_ab = a^H b and step 3), first-order perturbation of the
