@@ -173,6 +173,7 @@ KERNEL_SOURCES = {
     "setup_kernel": ["setup.cu", "rcscm_internal.cuh"],
     "naive_kernel": ["naive.cu", "rcscm_internal.cuh"],
     "adjoint_kernel": ["accel_common.cuh", "adjoint.cu", "rcscm_internal.cuh"],
+    "adjoint_setup_kernel": ["adjoint.cu", "rcscm_internal.cuh"],
     "ilrma_init_kernel": ["ilrma.cu", "ilrma.cuh", "rcscm_internal.cuh"],
     "accel1_kernel": ["accel1.cu", "accel_common.cuh", "dfloat.cuh", "rcscm_internal.cuh"],
     "naive_white_kernel": ["naive.cu", "rcscm_internal.cuh"],
