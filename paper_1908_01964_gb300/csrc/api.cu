@@ -333,9 +333,11 @@ int rcscm_create(rcscm_ctx** out, const rcscm_problem* probs, int n_probs, const
     if (!st) st = dalloc(c, &d.phi, Rz * 64);
     if (!st) st = dalloc(c, &d.a32, Rz * kMaxM);
     if (!st) st = dalloc(c, &d.b32, Rz * kMaxM);
-    if (!st) st = dalloc(c, &d.rp32, Rz * 64);
-    if (!st) st = dalloc(c, &d.wht32, Rz * 64);
-    if (!st) st = dalloc(c, &d.aw64, Rz * kMaxM);
+    // the naive rules' per-row inputs (the setup forms them only where they are allocated)
+    const bool printed = opt->rule == RCSCM_RULE_NAIVE_F64 || opt->rule == RCSCM_RULE_NAIVE_PRINTED;
+    if (!st && printed) st = dalloc(c, &d.rp32, Rz * 64);
+    if (!st && opt->rule == RCSCM_RULE_NAIVE) st = dalloc(c, &d.wht32, Rz * 64);
+    if (!st && opt->rule == RCSCM_RULE_NAIVE) st = dalloc(c, &d.aw64, Rz * kMaxM);
     if (!st) st = dalloc(c, &d.inv4, Sz);
     if (!st) st = dalloc(c, &d.kap, Sz);
     if (!st) st = dalloc(c, &d.rh, Sz);

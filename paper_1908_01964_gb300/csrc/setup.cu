@@ -602,10 +602,11 @@ setup_kernel(DevState d, int n_rows, double null_tol) {
     // FP32 copy of R' with the smallest eigenvalue set to zero (R' + lambda b b^H is then
     // exactly the model's R_i); formed in FP32 (mu_1 b b^H is a rounding-level term)
     const float mu1f = (float)mu1;
-    for (int e = l; e < MM; e += kGroupLanes) {
-        const int m = e / M, n = e % M;
-        d.rp32[(size_t)r * 64 + e] = csub(sA32[g][m][n], cscale(cmul(sb32[g][m], cconj(sb32[g][n])), mu1f));
-    }
+    if (d.rp32)
+        for (int e = l; e < MM; e += kGroupLanes) {
+            const int m = e / M, n = e % M;
+            d.rp32[(size_t)r * 64 + e] = csub(sA32[g][m][n], cscale(cmul(sb32[g][m], cconj(sb32[g][n])), mu1f));
+        }
     // Phi entries (kk, n): row 0 (R'^+ a)^H, rows 1..M-2 H L^H, row M-1 b^H (FP64, rounded once)
     float2* phi = d.phi + (size_t)r * 64;
     for (int e = l; e < MM; e += kGroupLanes) {
